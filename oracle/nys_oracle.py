@@ -1,0 +1,406 @@
+"""Plain FP64 CPU oracle of Nys-IP-PMM (arxiv 2404.14524) for separable QPs.
+
+TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the CPU-baseline
+leg of the benchmark import this module.  The product (the CUDA library and its
+Python binding) never imports, calls or links it, and it shares no code with
+the CUDA path: the two meet only through the seeded workload generators.
+
+The oracle is deliberately slow and literal.  Each function follows one passage
+of the paper, step by step and in the paper's notation, with library routines
+(matrix products, Cholesky, triangular solve, SVD) as the only building blocks.
+Readings taken where the paper is silent or garbled are marked READING.
+
+Scope: the practical method (Algorithm 6 driving the Mehrotra predictor-corrector
+of Algorithm 5 and the Newton solve of Algorithm 4) restricted to the
+all-non-negative case I = {1..n}, F = J = {} of problem (P)/(D).
+
+Pinning (tests/test_oracle_*.py): every function is checked against something
+other than itself -- the assembled 3x3-block Newton system (Eq. Newton),
+P_Nys from Eq. Nys_precond against P_Nys^{-1} from Eq. Nys_precond_inv, the
+Nystrom invariants of Section 2.3.2, a dense direct solve of the normal
+equations, brute-force active-set solutions of tiny QPs, hand-derived KKT
+points (tests/golden/), brute-force step-length scans, and numpy's spacing()
+for eps().  The PEU rule, the termination rule and the PCG tolerance are
+builder's readings of passages that only cite another paper; their constants
+are "parity unpinned" (they are made identical on both sides, not checked
+against the paper).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+# ---------------------------------------------------------------------------
+# Counter-based Gaussian test matrices (Algorithm 1, first step).
+#
+# READING: Algorithm 1 draws a fresh Gaussian Omega in every call.  Both the
+# oracle and the CUDA path draw entry (i, j) of Omega_k (IPM iteration k,
+# m x ell) from the SplitMix64 stream of Steele, Lea and Flood (OOPSLA 2014),
+# seeded with `seed`, at stream positions 2c and 2c+1 with
+# c = (k*ell + j)*m + i, turned into uniforms u = ((bits >> 11) + 1/2) 2^-53
+# and into one normal deviate by Box-Muller: sqrt(-2 ln u1) cos(2 pi u2).
+# ---------------------------------------------------------------------------
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_at(seed: int, pos: np.ndarray) -> np.ndarray:
+    """Output number `pos` (0-based) of the SplitMix64 stream whose state
+    starts at `seed`: the state after pos+1 increments by the golden gamma,
+    passed through the SplitMix64 finaliser."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (pos.astype(np.uint64) + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def gaussian_omega(seed: int, k: int, m: int, ell: int) -> np.ndarray:
+    """Omega_k, m x ell, float64 (row i, column j)."""
+    i = np.arange(m, dtype=np.uint64)[:, None]
+    j = np.arange(ell, dtype=np.uint64)[None, :]
+    c = (np.uint64(k) * np.uint64(ell) + j) * np.uint64(m) + i
+    b1 = splitmix64_at(seed, np.uint64(2) * c)
+    b2 = splitmix64_at(seed, np.uint64(2) * c + np.uint64(1))
+    u1 = ((b1 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    u2 = ((b2 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def eps_of(x: float) -> float:
+    """eps(x) of Algorithm 1, third step: the spacing of float64 numbers at x > 0,
+    2^(floor(log2 x) - 52).  READING: exactly Julia/MATLAB eps()."""
+    if not (x > 0.0) or not math.isfinite(x):
+        raise ValueError("eps_of needs a positive finite argument")
+    _, e = math.frexp(x)          # x = f 2^e, f in [0.5, 1)
+    return math.ldexp(1.0, e - 53)
+
+
+# ---------------------------------------------------------------------------
+# Normal-equations operator (Section 2.1.2, Eq. normal-eq).
+# ---------------------------------------------------------------------------
+
+def scaling_D(x: np.ndarray, z: np.ndarray, q: np.ndarray, rho: float) -> np.ndarray:
+    """Diagonal of (Q + Theta^{-1} + rho I)^{-1} with Theta = X Z^{-1}
+    (Section 2.1.2, below Eq. delta_z)."""
+    return 1.0 / (q + z / x + rho)
+
+
+def normal_matvec(A: np.ndarray, D: np.ndarray, delta: float, v: np.ndarray) -> np.ndarray:
+    """(N_k + delta I) v with N_k = A D A^T (Eq. normal-eq)."""
+    return A @ (D * (A.T @ v)) + delta * v
+
+
+def sketch(A: np.ndarray, D: np.ndarray, Omega: np.ndarray) -> np.ndarray:
+    """Y = N Omega with N = A D A^T (Algorithm 1, second step)."""
+    return A @ (D[:, None] * (A.T @ Omega))
+
+
+# ---------------------------------------------------------------------------
+# Randomized Nystrom approximation (Algorithm 1) and preconditioner
+# (Algorithm 2, Eq. Nys_precond_inv).
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class NystromFactor:
+    U: np.ndarray       # m x ell, orthonormal columns
+    lam: np.ndarray     # ell, descending, >= 0
+    nu: float           # the shift of Algorithm 1
+
+
+def nystrom_from_sketch(Y: np.ndarray, Omega: np.ndarray) -> NystromFactor:
+    """Algorithm 1, steps 3-8, given the sketch Y = N Omega."""
+    nu = eps_of(float(np.linalg.norm(Y, "fro")))          # step 3
+    Ynu = Y + nu * Omega                                  # step 4
+    G = Omega.T @ Ynu
+    G = 0.5 * (G + G.T)                                   # READING: symmetrise before chol
+    C = np.linalg.cholesky(G).T                           # step 5: upper C, G = C^T C
+    B = sla.solve_triangular(C, Ynu.T, trans="T", lower=False).T   # step 6: B = Ynu C^{-1}
+    Uh, S, _ = np.linalg.svd(B, full_matrices=False)      # step 7: thin SVD
+    lam = np.maximum(0.0, S * S - nu)                     # step 8
+    return NystromFactor(U=Uh, lam=lam, nu=nu)
+
+
+def nystrom(A: np.ndarray, D: np.ndarray, Omega: np.ndarray) -> NystromFactor:
+    """Algorithm 1 for N = A D A^T with a given Gaussian test matrix."""
+    return nystrom_from_sketch(sketch(A, D, Omega), Omega)
+
+
+def precond_inv_apply(F: NystromFactor, delta: float, r: np.ndarray) -> np.ndarray:
+    """P_Nys^{-1} r (Eq. Nys_precond_inv):
+    (lam_ell + delta) U (Lam + delta I)^{-1} U^T r + (I - U U^T) r.
+    READING: lam_ell is the last diagonal entry of the clipped, descending Lambda."""
+    lam_ell = F.lam[-1]
+    Utr = F.U.T @ r
+    return (lam_ell + delta) * (F.U @ (Utr / (F.lam + delta))) + r - F.U @ Utr
+
+
+def precond_apply(F: NystromFactor, delta: float, v: np.ndarray) -> np.ndarray:
+    """P_Nys v (Eq. Nys_precond): U (Lam + delta I) U^T v / (lam_ell + delta) + (I - U U^T) v."""
+    lam_ell = F.lam[-1]
+    Utv = F.U.T @ v
+    return (F.U @ ((F.lam + delta) * Utv)) / (lam_ell + delta) + v - F.U @ Utv
+
+
+# ---------------------------------------------------------------------------
+# Preconditioned CG on (N + delta I) dy = xi (Section 2.2).
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PCGResult:
+    x: np.ndarray
+    iters: int
+    res_norm: float       # recursive residual norm at exit
+    converged: bool
+
+
+def pcg(apply_M, apply_Pinv, rhs: np.ndarray, eta: float, maxit: int,
+        forced_iters: int | None = None) -> PCGResult:
+    """Textbook preconditioned CG from x0 = 0 (Golub & Van Loan, Alg. 11.5.1).
+
+    READING: stop at the top of an iteration once the recursive residual
+    satisfies ||r||_2 <= eta ||rhs||_2; `forced_iters` instead runs exactly that
+    many iterations (used to align iteration counts with another solver)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    bnorm = float(np.linalg.norm(rhs))
+    if bnorm == 0.0:
+        return PCGResult(x=x, iters=0, res_norm=0.0, converged=True)
+    zv = apply_Pinv(r)
+    p = zv.copy()
+    rz = float(r @ zv)
+    it = 0
+    limit = forced_iters if forced_iters is not None else maxit
+    while it < limit:
+        if forced_iters is None and float(np.linalg.norm(r)) <= eta * bnorm:
+            break
+        w = apply_M(p)
+        alpha = rz / float(p @ w)
+        x = x + alpha * p
+        r = r - alpha * w
+        zv = apply_Pinv(r)
+        rz_new = float(r @ zv)
+        beta = rz_new / rz
+        p = zv + beta * p
+        rz = rz_new
+        it += 1
+    rn = float(np.linalg.norm(r))
+    return PCGResult(x=x, iters=it, res_norm=rn, converged=rn <= eta * bnorm)
+
+
+def pcg_tolerance(mu: float) -> float:
+    """READING (the theory only asks for a residual of order mu_k, Prop. 3.2):
+    eta_k = max(1e-10, min(1e-2, 0.1 mu_k)), relative to ||xi||."""
+    return max(1e-10, min(1e-2, 0.1 * mu))
+
+
+# ---------------------------------------------------------------------------
+# Newton direction through the normal equations (Algorithm 4 with I = all).
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Direction:
+    dx: np.ndarray
+    dy: np.ndarray
+    dz: np.ndarray
+    pcg_iters: int
+    pcg_res: float
+
+
+def newton_direction(A, x, z, D, delta, r_d, r_p, r_xz, F, eta, maxit,
+                     forced_iters=None) -> Direction:
+    """Algorithm 4 for I = {1..n}:
+    xi_au = -X^{-1} r_xz;  xi = r_p + A D (r_d + xi_au);
+    (A D A^T + delta I) dy = xi by Nystrom PCG;
+    dx = D (A^T dy - r_d - xi_au);
+    dz = X^{-1} (r_xz - Z dx).
+    READING: Algorithm 4 prints dz = X^{-1} r_xz - Z dx; Eq. delta_z and the
+    third block row of Eq. Newton give X^{-1}(r_xz - Z dx), which is used."""
+    xi_au = -r_xz / x
+    xi = r_p + A @ (D * (r_d + xi_au))
+    res = pcg(lambda v: normal_matvec(A, D, delta, v),
+              lambda v: precond_inv_apply(F, delta, v),
+              xi, eta, maxit, forced_iters)
+    dy = res.x
+    dx = D * (A.T @ dy - r_d - xi_au)
+    dz = (r_xz - z * dx) / x
+    return Direction(dx=dx, dy=dy, dz=dz, pcg_iters=res.iters, pcg_res=res.res_norm)
+
+
+def step_length(v: np.ndarray, dv: np.ndarray) -> float:
+    """Fraction-to-boundary step (Eq. stepsize-p / stepsize-d):
+    0.995 min{1, min over dv_i < 0 of -v_i / dv_i}."""
+    neg = dv < 0.0
+    a = 1.0
+    if np.any(neg):
+        a = min(1.0, float(np.min(-v[neg] / dv[neg])))
+    return 0.995 * a
+
+
+# ---------------------------------------------------------------------------
+# Nys-IP-PMM driver (Algorithm 6 with Algorithm 5).
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Options:
+    tol: float = 1e-6
+    ell: int = 20
+    max_ipm_iter: int = 200
+    max_pcg_iter: int = 1000
+    seed: int = 0
+    rho0: float = 8.0            # Algorithm 6, second step
+    delta0: float = 8.0
+    reg_floor: float = 5e-10     # floor seen in Tables 7-8
+    forced_pcg: list | None = None   # per Newton solve: predictor, corrector, ...
+    forced_ipm: int | None = None
+
+
+@dataclasses.dataclass
+class IterRecord:
+    k: int
+    mu: float
+    rel_p: float
+    rel_d: float
+    rho: float
+    delta: float
+    nu: float
+    lam_max: float
+    lam_min: float
+    alpha_p: float
+    alpha_d: float
+    pcg_pred: int
+    pcg_corr: int
+
+
+@dataclasses.dataclass
+class Result:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    status: str               # "converged" | "max_iter"
+    ipm_iters: int
+    pcg_iters: list           # per Newton solve, in order
+    rel_p: float
+    rel_d: float
+    mu: float
+    rel_gap: float
+    rho: float
+    delta: float
+    trace: list
+
+
+def kkt_measures(A, b, c, q, x, y, z):
+    """READING of the termination test (Algorithm 3 tests absolute norms; the
+    experiments speak of relative infeasibilities): relative primal and dual
+    infeasibility and the duality measure mu = x^T z / n."""
+    rel_p = float(np.linalg.norm(A @ x - b)) / (1.0 + float(np.linalg.norm(b)))
+    rel_d = float(np.linalg.norm(c + q * x - A.T @ y - z)) / (1.0 + float(np.linalg.norm(c)))
+    mu = float(x @ z) / x.shape[0]
+    return rel_p, rel_d, mu
+
+
+def duality_gap(b, c, q, x, y):
+    """|pobj - dobj| / (1 + |pobj|) with the objectives of (P) and (D)."""
+    pobj = 0.5 * float(x @ (q * x)) + float(c @ x)
+    dobj = float(b @ y) - 0.5 * float(x @ (q * x))
+    return abs(pobj - dobj) / (1.0 + abs(pobj))
+
+
+def solve(A, b, c, q, x0, y0, z0, opt: Options) -> Result:
+    """Nys-IP-PMM from a given strictly interior start (Algorithm 6).
+
+    READING (start): the workloads supply a strictly feasible interior point
+    (x0, y0, z0); it is used as (x^0, y^0, z^0), with lambda^0 = y^0,
+    zeta^0 = x^0, rho_0 = delta_0 = 8 (Algorithm 6, second step).
+    READING (PEU, which the paper only cites): with
+    r_mu = |mu_{k+1} - mu_k| / max(mu_k, mu_{k+1}), if the primal infeasibility
+    ||b - A x|| fell to <= 0.95 of its previous value then lambda <- y and
+    delta <- max(floor, (1 - r_mu) delta), else delta <- max(floor,
+    (1 - 0.666 r_mu) delta); the same rule with the dual infeasibility
+    ||c + Q x - A^T y - z|| updates zeta <- x and rho."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    x, y, z = x0.astype(np.float64).copy(), y0.astype(np.float64).copy(), z0.astype(np.float64).copy()
+    lam_pmm, zeta = y.copy(), x.copy()
+    rho, delta = opt.rho0, opt.delta0
+    ell = min(opt.ell, m)
+    mu = float(x @ z) / n
+    trace, pcg_counts = [], []
+    status = "max_iter"
+    forced = list(opt.forced_pcg) if opt.forced_pcg is not None else None
+    k = 0
+    rel_p = rel_d = float("nan")
+    while True:
+        rel_p, rel_d, mu = kkt_measures(A, b, c, q, x, y, z)
+        if opt.forced_ipm is not None:
+            if k >= opt.forced_ipm:
+                status = "converged" if (rel_p <= opt.tol and rel_d <= opt.tol and mu <= opt.tol) else "forced"
+                break
+        elif rel_p <= opt.tol and rel_d <= opt.tol and mu <= opt.tol:
+            status = "converged"
+            break
+        if k >= opt.max_ipm_iter:
+            break
+        D = scaling_D(x, z, q, rho)
+        Omega = gaussian_omega(opt.seed, k, m, ell)
+        F = nystrom(A, D, Omega)
+        eta = pcg_tolerance(mu)
+        # Predictor (Algorithm 5, first step; Eq. predictor-RHS with I = all).
+        Ax, Aty = A @ x, A.T @ y
+        r_d = c + q * x - Aty - z + rho * (x - zeta)
+        r_p = b - Ax - delta * (y - lam_pmm)
+        r_xz = -x * z
+        fp = forced.pop(0) if forced else None
+        pred = newton_direction(A, x, z, D, delta, r_d, r_p, r_xz, F, eta, opt.max_pcg_iter, fp)
+        ap_bar = step_length(x, pred.dx)
+        ad_bar = step_length(z, pred.dz)
+        mu_aff = float((x + ap_bar * pred.dx) @ (z + ad_bar * pred.dz)) / n      # Eq. mu-aff
+        mu_tilde = mu_aff ** 3 / mu ** 2
+        # Corrector (Eq. corrector-RHS).
+        zero_n, zero_m = np.zeros(n), np.zeros(m)
+        r_xz_c = mu_tilde - pred.dx * pred.dz
+        fc = forced.pop(0) if forced else None
+        corr = newton_direction(A, x, z, D, delta, zero_n, zero_m, r_xz_c, F, eta, opt.max_pcg_iter, fc)
+        dx, dy, dz = pred.dx + corr.dx, pred.dy + corr.dy, pred.dz + corr.dz
+        alpha_p = step_length(x, dx)
+        alpha_d = step_length(z, dz)
+        nrp_old = float(np.linalg.norm(b - Ax))
+        nrd_old = float(np.linalg.norm(c + q * x - Aty - z))
+        x = x + alpha_p * dx
+        y = y + alpha_d * dy
+        z = z + alpha_d * dz
+        mu_new = float(x @ z) / n
+        pcg_counts += [pred.pcg_iters, corr.pcg_iters]
+        trace.append(IterRecord(k=k, mu=mu, rel_p=rel_p, rel_d=rel_d, rho=rho, delta=delta, nu=F.nu,
+                                lam_max=float(F.lam[0]), lam_min=float(F.lam[-1]),
+                                alpha_p=alpha_p, alpha_d=alpha_d,
+                                pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters))
+        # PEU (READING, see docstring).
+        r_mu = abs(mu_new - mu) / max(mu, mu_new)
+        nrp_new = float(np.linalg.norm(b - A @ x))
+        nrd_new = float(np.linalg.norm(c + q * x - A.T @ y - z))
+        if nrp_new <= 0.95 * nrp_old:
+            lam_pmm = y.copy()
+            delta = max(opt.reg_floor, (1.0 - r_mu) * delta)
+        else:
+            delta = max(opt.reg_floor, (1.0 - 0.666 * r_mu) * delta)
+        if nrd_new <= 0.95 * nrd_old:
+            zeta = x.copy()
+            rho = max(opt.reg_floor, (1.0 - r_mu) * rho)
+        else:
+            rho = max(opt.reg_floor, (1.0 - 0.666 * r_mu) * rho)
+        mu = mu_new
+        k += 1
+    return Result(x=x, y=y, z=z, status=status, ipm_iters=k, pcg_iters=pcg_counts,
+                  rel_p=rel_p, rel_d=rel_d, mu=mu, rel_gap=duality_gap(b, c, q, x, y),
+                  rho=rho, delta=delta, trace=trace)
+
+
+def solve_qp(qp, opt: Options) -> Result:
+    """Convenience wrapper over a workload record with fields A, b, c, q, x0, y0, z0."""
+    return solve(qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0, opt)

@@ -1,0 +1,176 @@
+"""Seeded synthetic separable-QP workloads.
+
+This module only builds problem data: it holds none of the solver's arithmetic,
+so both the CUDA path and the CPU oracle can take their inputs from it.
+
+Every workload is a primal-dual pair (P)/(D) of Section 1 with diagonal
+Q = diag(q) >= 0 and x >= 0.  The paper's own workloads (SVM datasets of
+Table 3, the portfolio generator of Section 5.1) are not reproducible here,
+so these generators stand in for them with dense constraint matrices of a
+prescribed singular-value spectrum:
+
+    A = U diag(sigma) V^T,  U = Haar m x m orthogonal,  V = Haar n x m
+    (orthonormal columns), built as the sign-fixed Q factor of a Gaussian.
+
+The feasible start is built so that the start point is strictly interior and
+primal/dual feasible: x0 ~ U[0.5, 1.5], b = A x0, y0 ~ N(0, 1),
+z0 ~ U[0, 1] clamped to >= 1e-3, c = A^T y0 + z0 - Q x0.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+Z0_FLOOR = 1e-3
+
+
+@dataclasses.dataclass
+class QP:
+    """One separable QP (P)/(D) with a feasible interior start point (all float64,
+    A row-major m x n)."""
+    A: np.ndarray
+    b: np.ndarray
+    c: np.ndarray
+    q: np.ndarray
+    x0: np.ndarray
+    y0: np.ndarray
+    z0: np.ndarray
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[1]
+
+
+def haar_columns(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    """rows x cols matrix with orthonormal columns, Haar-distributed (QR of a
+    Gaussian with the signs of R's diagonal folded into Q)."""
+    g = rng.standard_normal((rows, cols))
+    qf, r = np.linalg.qr(g, mode="reduced")
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1.0
+    return qf * s[None, :]
+
+
+def spectrum_matrix(rng: np.random.Generator, m: int, n: int, sigma: np.ndarray) -> np.ndarray:
+    """A = U diag(sigma) V^T with Haar factors; requires m <= n, len(sigma) == m."""
+    assert m <= n and sigma.shape == (m,)
+    u = haar_columns(rng, m, m)
+    v = haar_columns(rng, n, m)
+    return np.ascontiguousarray((u * sigma[None, :]) @ v.T)
+
+
+def feasible_qp(rng: np.random.Generator, A: np.ndarray, q: np.ndarray, name: str = "") -> QP:
+    """Attach the feasible-start generator to a constraint matrix and diag(Q)."""
+    m, n = A.shape
+    x0 = rng.uniform(0.5, 1.5, n)
+    y0 = rng.standard_normal(m)
+    z0 = np.maximum(rng.uniform(0.0, 1.0, n), Z0_FLOOR)
+    b = A @ x0
+    c = A.T @ y0 + z0 - q * x0
+    return QP(A=A, b=b, c=c, q=q, x0=x0, y0=y0, z0=z0, name=name)
+
+
+def spectral_qp(seed: int, m: int, n: int, sigma_kind: str, q_kind: str = "uniform") -> QP:
+    """Single dense QP with a prescribed spectrum.
+
+    sigma_kind: "inv" (sigma_i = 1/i), "pow0.8" (sigma_i = i^-0.8),
+                "exp200" (sigma_i = exp(-i/200) + 1e-3).
+    q_kind:     "uniform" (q ~ U[0,1]), "half_zero" (50% zeros, rest U[0,1]),
+                "uniform_0.1" (q ~ U[0.1, 1]), "zero" (an LP).
+    """
+    rng = np.random.default_rng(seed)
+    i = np.arange(1, m + 1, dtype=np.float64)
+    if sigma_kind == "inv":
+        sigma = 1.0 / i
+    elif sigma_kind == "pow0.8":
+        sigma = i ** -0.8
+    elif sigma_kind == "exp200":
+        sigma = np.exp(-i / 200.0) + 1e-3
+    else:
+        raise ValueError(sigma_kind)
+    A = spectrum_matrix(rng, m, n, sigma)
+    q = make_q(rng, n, q_kind)
+    return feasible_qp(rng, A, q, name=f"spectral-{sigma_kind}-{m}x{n}-s{seed}")
+
+
+def make_q(rng: np.random.Generator, n: int, q_kind: str) -> np.ndarray:
+    if q_kind == "uniform":
+        return rng.uniform(0.0, 1.0, n)
+    if q_kind == "half_zero":
+        q = rng.uniform(0.0, 1.0, n)
+        q[rng.permutation(n)[: n // 2]] = 0.0
+        return q
+    if q_kind == "uniform_0.1":
+        return rng.uniform(0.1, 1.0, n)
+    if q_kind == "zero":
+        return np.zeros(n)
+    raise ValueError(q_kind)
+
+
+def gaussian_qp(seed: int, m: int, n: int, q_kind: str = "uniform_0.1") -> QP:
+    """Dense QP with i.i.d. N(0, 1/n) constraint entries (the differentiation
+    workload: 64 QPs of 512 x 2048 with q ~ U[0.1, 1])."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) / np.sqrt(n)
+    q = make_q(rng, n, q_kind)
+    return feasible_qp(rng, A, q, name=f"gaussian-{m}x{n}-s{seed}")
+
+
+def low_rank_qp(seed: int, m: int, n: int, rank: int, q_kind: str = "uniform") -> QP:
+    """QP whose A has exact rank `rank` < m (A A^T singular); b is still
+    consistent because b = A x0.  Used where N = A D A^T must have rank <= ell."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n)) / np.sqrt(n)
+    q = make_q(rng, n, q_kind)
+    return feasible_qp(rng, A, q, name=f"lowrank{rank}-{m}x{n}-s{seed}")
+
+
+# ---------------------------------------------------------------------------
+# Named workloads with the shapes of the five benchmark configurations.
+# ---------------------------------------------------------------------------
+
+def workload_small(seed: int = 1235) -> QP:
+    """m=200, n=500, sigma_i = 1/i, q ~ U[0,1]; solved with ell=20, tol 1e-6."""
+    return spectral_qp(seed, 200, 500, "inv", "uniform")
+
+
+def workload_fp64(seed: int = 1236) -> QP:
+    """m=5000, n=20000, sigma_i = i^-0.8, q half zeros; ell=100, tol 1e-8."""
+    return spectral_qp(seed, 5000, 20000, "pow0.8", "half_zero")
+
+
+def workload_fp64_scaled(seed: int = 1236, m: int = 1000, n: int = 4000) -> QP:
+    """Scaled-down shape of the m=5000, n=20000 workload (same recipe)."""
+    return spectral_qp(seed, m, n, "pow0.8", "half_zero")
+
+
+def workload_precision_scaled(seed: int = 1237, m: int = 2000, n: int = 10000) -> QP:
+    """Scaled-down shape of the m=20000, n=100000 precision workload
+    (sigma_i = exp(-i/200) + 1e-3, q ~ U[0,1])."""
+    return spectral_qp(seed, m, n, "exp200", "uniform")
+
+
+def workload_batch(seed: int = 1238, count: int = 256, m_lo: int = 64, m_hi: int = 1024):
+    """`count` QPs with m ~ U{m_lo..m_hi}, n ~ U{4m..8m}, sigma_i = 1/i,
+    q ~ U[0,1]; per-QP ell = min(32, m // 4)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(count):
+        m = int(rng.integers(m_lo, m_hi + 1))
+        n = int(rng.integers(4 * m, 8 * m + 1))
+        out.append(spectral_qp(seed * 1000 + t, m, n, "inv", "uniform"))
+    return out
+
+
+def workload_diff(seed: int = 1239, count: int = 64, m: int = 512, n: int = 2048):
+    """`count` Gaussian QPs (m x n) with q ~ U[0.1, 1] and targets x_t ~ U[0,1]
+    for the loss L = ||x* - x_t||^2."""
+    rng = np.random.default_rng(seed)
+    qps = [gaussian_qp(seed * 1000 + t, m, n, "uniform_0.1") for t in range(count)]
+    targets = [rng.uniform(0.0, 1.0, n) for _ in range(count)]
+    return qps, targets
