@@ -1,0 +1,210 @@
+/*
+ * nys.h -- C ABI of the GB300 (sm_103a) Nys-IP-PMM normal-equations solver.
+ *
+ * The library solves separable convex QPs (Section 1, problems (P)/(D)):
+ *     min 1/2 x^T Q x + c^T x   s.t.  A x = b,  x >= 0,     Q = diag(q), q >= 0,
+ * by the randomized-Nystrom-preconditioned IP-PMM of arxiv 2404.14524
+ * (Algorithm 6 with the predictor-corrector of Algorithm 5 and the Newton
+ * solve of Algorithm 4).  Every step of the solve runs in this library's CUDA
+ * kernels; the caller only provides memory and a CUDA stream.
+ *
+ * Conventions for every entry point below:
+ *  - A is dense and row-major, m x n, leading dimension lda >= n (elements).
+ *  - Tall m x ell panels (Omega, Y, U) are column-major with leading
+ *    dimension ld >= m (elements).
+ *  - "device" pointers are CUDA device (or managed) memory on the handle's
+ *    device; "host" pointers are ordinary host memory.  The caller owns every
+ *    pointer it passes; the handle owns only its internal workspace.
+ *  - All work is issued on the handle's stream.  Entry points that return a
+ *    scalar through a host pointer synchronise that stream before returning.
+ *  - Return value: NYS_OK (0), a negative error, or a positive warning.  No
+ *    entry point aborts, traps or throws; after an error the message is
+ *    available from nys_last_error(h).  Invalid sizes or NULL pointers give
+ *    NYS_ERR_ARG before any device work is issued.
+ */
+#ifndef NYS_H
+#define NYS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nys_solver* nys_handle;
+
+typedef enum {
+    NYS_OK = 0,
+    NYS_ERR_ARG = -1,             /* invalid argument (size, pointer, dtype, ell)     */
+    NYS_ERR_CUDA = -2,            /* a CUDA runtime call failed                       */
+    NYS_ERR_NUMERIC = -3,         /* NaN/Inf met in an iterate or a reduction         */
+    NYS_ERR_CORE_BREAKDOWN = -4,  /* chol(Omega^T Y_nu) hit a non-positive pivot      */
+    NYS_ERR_TIMEOUT = -5,         /* a bounded device-side wait expired               */
+    NYS_ERR_NOMEM = -6,           /* workspace allocation failed / problem too large  */
+    NYS_WARN_MAXITER = 1,         /* IPM reached max_ipm_iter before the tolerance    */
+    NYS_WARN_PCG_MAXITER = 2      /* some PCG solve stopped at max_pcg_iter           */
+} nys_status;
+
+typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2, NYS_FP8E4M3 = 3 } nys_dtype;
+
+/* Solver options.  Defaults (nys_default_options): tol 1e-6, ell 20,
+ * max_ipm_iter 200, max_pcg_iter 1000, seed 0, rho0 = delta0 = 8 (Algorithm 6,
+ * second step), reg_floor 5e-10 (the floor seen in Tables 7-8). */
+typedef struct {
+    double tol;                   /* relative KKT tolerance of the termination test  */
+    int ell;                      /* Nystrom sketch size (clamped to m)               */
+    int max_ipm_iter;
+    int max_pcg_iter;
+    unsigned long long seed;      /* key of the counter-based Gaussian stream         */
+    int precision_mode;           /* 0 = FP64 form (A must be NYS_F64)                */
+    double rho0, delta0, reg_floor;
+    /* Parity mode (optional, host arrays): run exactly forced_pcg_iters[s] PCG
+     * iterations in Newton solve s (predictor, corrector, predictor, ...), and
+     * exactly forced_ipm_iters IPM iterations when >= 0. */
+    const int* forced_pcg_iters;
+    int n_forced_pcg;
+    int forced_ipm_iters;
+} nys_options;
+
+/* One QP.  With host == 0 all pointers are device pointers; with host == 1
+ * they are host pointers and nys_solve stages them to the device itself
+ * (copies included in nys_result.seconds).  x0, y0, z0 is the strictly
+ * interior start point (x0 > 0, z0 > 0).
+ * Warm start (resume from a saved state): lam0 and zeta0 are the PMM
+ * estimates lambda, zeta (NULL = y0, x0 as in Algorithm 6), the options'
+ * rho0/delta0 carry rho and delta, and k0 is the index of the first IPM
+ * iteration (it selects the Gaussian test matrix Omega_k). */
+typedef struct {
+    int m, n;
+    int a_dtype;                  /* nys_dtype of A                                   */
+    const void* A;                /* m x n row-major                                  */
+    long long lda;
+    const double *b, *c, *q;      /* m, n, n                                          */
+    const double *x0, *y0, *z0;   /* n, m, n                                          */
+    int host;
+    const double *lam0, *zeta0;   /* m, n, or NULL                                    */
+    int k0;
+} nys_problem;
+
+/* Result.  x, y, z are caller-allocated outputs (n, m, n) in the same memory
+ * space as the problem (device, or host when problem.host == 1).  On an error
+ * they hold the last complete iterate.  lam, zeta (m, n; NULL = not wanted)
+ * receive the final PMM estimates, which with rho/delta and ipm_iters make a
+ * resumable state. */
+typedef struct {
+    double *x, *y, *z;
+    double *lam, *zeta;
+    int status;                   /* nys_status of the solve                          */
+    int ipm_iters;
+    int pcg_iters_total;
+    int refine_steps;
+    double rel_primal;            /* ||Ax - b|| / (1 + ||b||)                          */
+    double rel_dual;              /* ||c + Qx - A^T y - z|| / (1 + ||c||)              */
+    double mu;                    /* x^T z / n                                         */
+    double rel_gap;               /* |pobj - dobj| / (1 + |pobj|)                      */
+    double rho, delta;            /* final PMM regularisation                          */
+    double seconds;               /* wall time inside nys_solve                        */
+    int* pcg_log;                 /* optional host array: PCG iterations per Newton   */
+    int pcg_log_cap;              /*   solve, in order (capacity in entries)           */
+    int pcg_log_len;              /* entries written                                   */
+} nys_result;
+
+/* Fill *opt with the defaults listed above. */
+void nys_default_options(nys_options* opt);
+
+/* Create a solver handle for problems up to max_m x max_n.  cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream).  Allocates the workspace
+ * (O(max_m*ell + max_n*ell + ell^2) doubles plus split-reduction buffers) on
+ * the current device.  Errors: NYS_ERR_ARG, NYS_ERR_NOMEM, NYS_ERR_CUDA. */
+int nys_create(nys_handle* h, const nys_options* opt, int max_m, int max_n, int max_batch,
+               void* cuda_stream);
+
+/* Solve one QP with Algorithm 6 (IP-PMM, Nystrom PCG for every Newton system).
+ * Termination: rel_primal, rel_dual and mu all <= tol.  Returns the status
+ * also stored in r->status. */
+int nys_solve(nys_handle h, const nys_problem* p, nys_result* r);
+
+int nys_destroy(nys_handle h);
+
+/* Message of the last error recorded on h (static storage owned by h). */
+const char* nys_last_error(nys_handle h);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all handles; a counter for instrumentation, not a synchronisation). */
+unsigned long long nys_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points (device pointers).  Each is one step of the solve,
+ * exposed so that it can be called and checked on its own.
+ * ------------------------------------------------------------------------- */
+
+/* D = (Q + Theta^{-1} + rho I)^{-1} with Theta = X Z^{-1}, i.e.
+ * D_j = 1 / (q_j + z_j / x_j + rho)  (Section 2.1.2, below Eq. delta_z).
+ * x, z, q, D: device, length n.  x > 0 is required (not checked). */
+int nys_scaling(nys_handle h, int n, const double* x, const double* z, const double* q,
+                double rho, double* D);
+
+/* out = (N + delta I) v with N = A diag(D) A^T (Eq. normal-eq): one streaming
+ * pass of A for t = D .* (A^T v) and one for A t.  A: device, a_dtype must be
+ * NYS_F64.  D: device n; v, out: device m (out must not alias v). */
+int nys_normal_matvec(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
+                      const double* D, double delta, const double* v, double* out);
+
+/* Omega_k (m x ell, leading dimension ld): entry (i, j) is the standard normal
+ * deviate of Algorithm 1's first step drawn from the SplitMix64 stream of
+ * Steele, Lea and Flood (2014) keyed by `seed`, at stream positions 2c and
+ * 2c + 1 with c = (k*ell + j)*m + i, via u = ((bits >> 11) + 1/2) 2^-53 and
+ * Box-Muller sqrt(-2 ln u1) cos(2 pi u2).  Omega: device. */
+int nys_gaussian(nys_handle h, unsigned long long seed, int k, int m, int ell, double* Omega,
+                 int ld);
+
+/* Sketch Y = N Omega = A (D .* (A^T Omega)) (Algorithm 1, second step).
+ * Omega, Y: device m x ell (column-major, leading dimension ld); D: device n. */
+int nys_sketch(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
+               const double* D, int ell, const double* Omega, double* Y, int ld);
+
+/* Nystrom factor from a sketch (Algorithm 1, steps 3-8): nu = eps(||Y||_F),
+ * Y_nu = Y + nu Omega, C = chol(Omega^T Y_nu) (upper, after symmetrising),
+ * B = Y_nu C^{-1}, thin SVD B = U Sigma V^T, lam = max(0, Sigma^2 - nu),
+ * sorted descending.  Y, Omega: device m x ell inputs (not modified);
+ * U: device m x ell output (same ld); lam: device ell output; *nu: host.
+ * Errors: NYS_ERR_CORE_BREAKDOWN if the Cholesky meets a pivot <= 0. */
+int nys_nystrom(nys_handle h, int m, int ell, const double* Y, const double* Omega, int ld,
+                double* U, double* lam, double* nu);
+
+/* out = P_Nys^{-1} r (Eq. Nys_precond_inv):
+ * (lam_ell + delta) U (Lam + delta I)^{-1} U^T r + (I - U U^T) r, with
+ * lam_ell the last (smallest) entry of lam.  U: device m x ell (ld);
+ * lam: device ell; r, out: device m (out must not alias r). */
+int nys_precond_apply(nys_handle h, int m, int ell, const double* U, int ld, const double* lam,
+                      double delta, const double* r, double* out);
+
+/* Preconditioned CG for (N + delta I) dy = xi from dy = 0 (Section 2.2 with
+ * P_Nys), N = A diag(D) A^T.  Stops at the top of an iteration once the
+ * recursive residual satisfies ||r|| <= eta ||xi||, or after max_iter
+ * iterations; forced_iters >= 0 runs exactly that many.  *iters and
+ * *res_norm (host) receive the iteration count and final ||r||.
+ * Returns NYS_WARN_PCG_MAXITER if the tolerance was not met. */
+int nys_pcg(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
+            const double* D, double delta, int ell, const double* U, int ld, const double* lam,
+            const double* xi, double* dy, double eta, int max_iter, int forced_iters,
+            int* iters, double* res_norm);
+
+/* Newton direction through the normal equations (Algorithm 4 with I = all):
+ * xi_au = -X^{-1} r_xz; xi = r_p + A D (r_d + xi_au); (N + delta I) dy = xi by
+ * the PCG above; dx = D (A^T dy - r_d - xi_au); dz = X^{-1} (r_xz - Z dx).
+ * Vectors: device; r_d, r_xz, x, z, D, dx, dz length n; r_p, dy length m. */
+int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
+               const double* x, const double* z, const double* D, double delta,
+               const double* r_d, const double* r_p, const double* r_xz,
+               int ell, const double* U, int ld, const double* lam,
+               double eta, int max_iter, int forced_iters,
+               double* dx, double* dy, double* dz, int* iters);
+
+/* Fraction-to-boundary step (Eq. stepsize-p / stepsize-d):
+ * *alpha = 0.995 min{1, min over dv_i < 0 of -v_i / dv_i}.
+ * v, dv: device length n; *alpha: host. */
+int nys_step_length(nys_handle h, int n, const double* v, const double* dv, double* alpha);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NYS_H */

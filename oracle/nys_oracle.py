@@ -275,6 +275,7 @@ class IterRecord:
     alpha_d: float
     pcg_pred: int
     pcg_corr: int
+    state: tuple | None = None
 
 
 @dataclasses.dataclass
@@ -311,12 +312,17 @@ def duality_gap(b, c, q, x, y):
     return abs(pobj - dobj) / (1.0 + abs(pobj))
 
 
-def solve(A, b, c, q, x0, y0, z0, opt: Options) -> Result:
+def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int = 0,
+          record: bool = False) -> Result:
     """Nys-IP-PMM from a given strictly interior start (Algorithm 6).
 
     READING (start): the workloads supply a strictly feasible interior point
     (x0, y0, z0); it is used as (x^0, y^0, z^0), with lambda^0 = y^0,
     zeta^0 = x^0, rho_0 = delta_0 = 8 (Algorithm 6, second step).
+    Warm start (resume): lam0, zeta0 replace lambda^0, zeta^0, opt.rho0 and
+    opt.delta0 carry the PMM parameters, and k0 is the index of the first IPM
+    iteration (it selects Omega_k).  With record=True every trace entry also
+    holds the state (x, y, z, lambda, zeta) at the top of its iteration.
     READING (PEU, which the paper only cites): with
     r_mu = |mu_{k+1} - mu_k| / max(mu_k, mu_{k+1}), if the primal infeasibility
     ||b - A x|| fell to <= 0.95 of its previous value then lambda <- y and
@@ -326,7 +332,8 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options) -> Result:
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     x, y, z = x0.astype(np.float64).copy(), y0.astype(np.float64).copy(), z0.astype(np.float64).copy()
-    lam_pmm, zeta = y.copy(), x.copy()
+    lam_pmm = y.copy() if lam0 is None else np.asarray(lam0, dtype=np.float64).copy()
+    zeta = x.copy() if zeta0 is None else np.asarray(zeta0, dtype=np.float64).copy()
     rho, delta = opt.rho0, opt.delta0
     ell = min(opt.ell, m)
     mu = float(x @ z) / n
@@ -346,8 +353,10 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options) -> Result:
             break
         if k >= opt.max_ipm_iter:
             break
+        state_lam, state_zeta = lam_pmm.copy(), zeta.copy()
+        x_top, y_top, z_top = x.copy(), y.copy(), z.copy()
         D = scaling_D(x, z, q, rho)
-        Omega = gaussian_omega(opt.seed, k, m, ell)
+        Omega = gaussian_omega(opt.seed, k0 + k, m, ell)
         F = nystrom(A, D, Omega)
         eta = pcg_tolerance(mu)
         # Predictor (Algorithm 5, first step; Eq. predictor-RHS with I = all).
@@ -376,10 +385,13 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options) -> Result:
         z = z + alpha_d * dz
         mu_new = float(x @ z) / n
         pcg_counts += [pred.pcg_iters, corr.pcg_iters]
-        trace.append(IterRecord(k=k, mu=mu, rel_p=rel_p, rel_d=rel_d, rho=rho, delta=delta, nu=F.nu,
-                                lam_max=float(F.lam[0]), lam_min=float(F.lam[-1]),
-                                alpha_p=alpha_p, alpha_d=alpha_d,
-                                pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters))
+        rec = IterRecord(k=k0 + k, mu=mu, rel_p=rel_p, rel_d=rel_d, rho=rho, delta=delta, nu=F.nu,
+                         lam_max=float(F.lam[0]), lam_min=float(F.lam[-1]),
+                         alpha_p=alpha_p, alpha_d=alpha_d,
+                         pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters)
+        if record:
+            rec.state = (x_top, y_top, z_top, state_lam, state_zeta)
+        trace.append(rec)
         # PEU (READING, see docstring).
         r_mu = abs(mu_new - mu) / max(mu, mu_new)
         nrp_new = float(np.linalg.norm(b - A @ x))
@@ -401,6 +413,6 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options) -> Result:
                   rho=rho, delta=delta, trace=trace)
 
 
-def solve_qp(qp, opt: Options) -> Result:
+def solve_qp(qp, opt: Options, **kw) -> Result:
     """Convenience wrapper over a workload record with fields A, b, c, q, x0, y0, z0."""
-    return solve(qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0, opt)
+    return solve(qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0, opt, **kw)

@@ -1,0 +1,331 @@
+"""Thin ctypes binding of the C ABI in include/nys.h.
+
+Argument marshalling only: every step runs in libnys.so's CUDA kernels.
+Functions keep the C names (nys_create, nys_solve, ...).  Tensors are
+torch tensors on the handle's CUDA device (float64, contiguous); tall
+m x ell panels are passed as (ell, m) row-major tensors, i.e. column-major
+m x ell with leading dimension m.  The binding raises NysError when the
+library reports an error and fails loudly (ImportError) when libnys.so has
+not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnys.so")
+
+NYS_OK = 0
+NYS_ERR_ARG = -1
+NYS_ERR_CUDA = -2
+NYS_ERR_NUMERIC = -3
+NYS_ERR_CORE_BREAKDOWN = -4
+NYS_ERR_TIMEOUT = -5
+NYS_ERR_NOMEM = -6
+NYS_WARN_MAXITER = 1
+NYS_WARN_PCG_MAXITER = 2
+NYS_F64, NYS_F32, NYS_BF16, NYS_FP8E4M3 = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "ok", -1: "bad argument", -2: "CUDA error", -3: "numeric error",
+                -4: "core breakdown", -5: "device wait timed out", -6: "out of memory",
+                1: "IPM max iterations", 2: "PCG max iterations"}
+
+
+class NysError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("ell", ctypes.c_int), ("max_ipm_iter", ctypes.c_int),
+                ("max_pcg_iter", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("precision_mode", ctypes.c_int), ("rho0", ctypes.c_double),
+                ("delta0", ctypes.c_double), ("reg_floor", ctypes.c_double),
+                ("forced_pcg_iters", ctypes.POINTER(ctypes.c_int)), ("n_forced_pcg", ctypes.c_int),
+                ("forced_ipm_iters", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("a_dtype", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_longlong),
+                ("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("x0", ctypes.c_void_p), ("y0", ctypes.c_void_p), ("z0", ctypes.c_void_p),
+                ("host", ctypes.c_int), ("lam0", ctypes.c_void_p), ("zeta0", ctypes.c_void_p),
+                ("k0", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("lam", ctypes.c_void_p), ("zeta", ctypes.c_void_p),
+                ("status", ctypes.c_int), ("ipm_iters", ctypes.c_int),
+                ("pcg_iters_total", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("rel_primal", ctypes.c_double), ("rel_dual", ctypes.c_double),
+                ("mu", ctypes.c_double), ("rel_gap", ctypes.c_double), ("rho", ctypes.c_double),
+                ("delta", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
+                ("pcg_log_len", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_LL = ctypes.c_longlong
+
+_SIGS = {
+    "nys_default_options": (None, [ctypes.POINTER(Options)]),
+    "nys_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Options), _I, _I, _I, _P]),
+    "nys_solve": (_I, [_P, ctypes.POINTER(Problem), ctypes.POINTER(Result)]),
+    "nys_destroy": (_I, [_P]),
+    "nys_last_error": (ctypes.c_char_p, [_P]),
+    "nys_kernel_launches": (ctypes.c_ulonglong, []),
+    "nys_scaling": (_I, [_P, _I, _P, _P, _P, _D, _P]),
+    "nys_normal_matvec": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _P, _P]),
+    "nys_gaussian": (_I, [_P, ctypes.c_ulonglong, _I, _I, _I, _P, _I]),
+    "nys_sketch": (_I, [_P, _I, _I, _I, _P, _LL, _P, _I, _P, _P, _I]),
+    "nys_nystrom": (_I, [_P, _I, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_D)]),
+    "nys_precond_apply": (_I, [_P, _I, _I, _P, _I, _P, _D, _P, _P]),
+    "nys_pcg": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _I, _P, _I, _P, _P, _P, _D, _I, _I,
+                     ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nys_newton": (_I, [_P, _I, _I, _I, _P, _LL, _P, _P, _P, _D, _P, _P, _P, _I, _P, _I, _P, _D,
+                        _I, _I, _P, _P, _P, ctypes.POINTER(_I)]),
+    "nys_step_length": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
+}
+
+
+def lib():
+    """Load libnys.so (built by paper_2404_14524_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2404_14524_gb300.build` "
+                              "(the solver has no non-CUDA fallback)")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _f64(t, name, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} must be on {device}")
+    return t
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Handle:
+    """Owner of one nys_handle (workspace on the current CUDA device, bound to a stream)."""
+
+    def __init__(self, max_m: int, max_n: int, ell: int = 20, tol: float = 1e-6, seed: int = 0,
+                 max_ipm_iter: int = 200, max_pcg_iter: int = 1000, forced_pcg=None,
+                 forced_ipm: int = -1, stream=None, max_batch: int = 0, **kw):
+        l = lib()
+        o = Options()
+        l.nys_default_options(ctypes.byref(o))
+        o.tol, o.ell, o.seed = tol, ell, seed
+        o.max_ipm_iter, o.max_pcg_iter = max_ipm_iter, max_pcg_iter
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self._forced = None
+        if forced_pcg is not None:
+            self._forced = (ctypes.c_int * len(forced_pcg))(*[int(v) for v in forced_pcg])
+            o.forced_pcg_iters = self._forced
+            o.n_forced_pcg = len(forced_pcg)
+        o.forced_ipm_iters = forced_ipm
+        self.options = o
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = l.nys_create(ctypes.byref(h), ctypes.byref(o), max_m, max_n, max_batch,
+                          ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise NysError(rc, "nys_create failed")
+        self.h = h
+        self.max_m, self.max_n, self.ell = max_m, max_n, min(ell, max_m)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc: int, allow_warn: bool = True):
+        if rc < 0 or (rc > 0 and not allow_warn):
+            raise NysError(rc, lib().nys_last_error(self.h).decode())
+        return rc
+
+
+# ------------------------------------------------------------------ entry points
+
+def nys_create(max_m, max_n, **kw) -> Handle:
+    return Handle(max_m, max_n, **kw)
+
+
+def nys_destroy(h: Handle):
+    h.close()
+
+
+def nys_last_error(h: Handle) -> str:
+    return lib().nys_last_error(h.h).decode()
+
+
+def nys_kernel_launches() -> int:
+    return int(lib().nys_kernel_launches())
+
+
+def nys_scaling(h: Handle, x, z, q, rho: float, D=None):
+    n = x.numel()
+    D = torch.empty_like(x) if D is None else D
+    h.check(lib().nys_scaling(h.h, n, _ptr(_f64(x, "x")), _ptr(_f64(z, "z")), _ptr(_f64(q, "q")),
+                              float(rho), _ptr(_f64(D, "D"))))
+    return D
+
+
+def nys_normal_matvec(h: Handle, A, D, delta: float, v, out=None):
+    m, n = A.shape
+    out = torch.empty_like(v) if out is None else out
+    h.check(lib().nys_normal_matvec(h.h, m, n, NYS_F64, _ptr(_f64(A, "A")), A.stride(0),
+                                    _ptr(_f64(D, "D")), float(delta), _ptr(_f64(v, "v")),
+                                    _ptr(_f64(out, "out"))))
+    return out
+
+
+def nys_gaussian(h: Handle, seed: int, k: int, m: int, ell: int, out=None):
+    out = torch.empty((ell, m), dtype=torch.float64, device=h.device) if out is None else out
+    h.check(lib().nys_gaussian(h.h, seed, k, m, ell, _ptr(_f64(out, "Omega")), out.shape[1]))
+    return out
+
+
+def nys_sketch(h: Handle, A, D, Omega, out=None):
+    m, n = A.shape
+    ell = Omega.shape[0]
+    out = torch.empty_like(Omega) if out is None else out
+    h.check(lib().nys_sketch(h.h, m, n, NYS_F64, _ptr(_f64(A, "A")), A.stride(0), _ptr(_f64(D, "D")),
+                             ell, _ptr(_f64(Omega, "Omega")), _ptr(_f64(out, "Y")), Omega.shape[1]))
+    return out
+
+
+def nys_nystrom(h: Handle, Y, Omega):
+    ell, ld = Y.shape
+    m = ld
+    U = torch.empty_like(Y)
+    lam = torch.empty(ell, dtype=torch.float64, device=Y.device)
+    nu = ctypes.c_double()
+    h.check(lib().nys_nystrom(h.h, m, ell, _ptr(_f64(Y, "Y")), _ptr(_f64(Omega, "Omega")), ld,
+                              _ptr(U), _ptr(lam), ctypes.byref(nu)))
+    return U, lam, nu.value
+
+
+def nys_precond_apply(h: Handle, U, lam, delta: float, r, out=None):
+    ell, m = U.shape
+    out = torch.empty_like(r) if out is None else out
+    h.check(lib().nys_precond_apply(h.h, m, ell, _ptr(_f64(U, "U")), m, _ptr(_f64(lam, "lam")),
+                                    float(delta), _ptr(_f64(r, "r")), _ptr(_f64(out, "out"))))
+    return out
+
+
+def nys_pcg(h: Handle, A, D, delta: float, U, lam, xi, eta: float, max_iter: int, forced: int = -1,
+            out=None):
+    m, n = A.shape
+    ell = U.shape[0]
+    out = torch.empty_like(xi) if out is None else out
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    rc = lib().nys_pcg(h.h, m, n, NYS_F64, _ptr(_f64(A, "A")), A.stride(0), _ptr(_f64(D, "D")),
+                       float(delta), ell, _ptr(_f64(U, "U")), U.shape[1], _ptr(_f64(lam, "lam")),
+                       _ptr(_f64(xi, "xi")), _ptr(_f64(out, "dy")), float(eta), int(max_iter),
+                       int(forced), ctypes.byref(it), ctypes.byref(res))
+    h.check(rc)
+    return out, it.value, res.value, rc
+
+
+def nys_newton(h: Handle, A, x, z, D, delta, r_d, r_p, r_xz, U, lam, eta, max_iter, forced=-1):
+    m, n = A.shape
+    ell = U.shape[0]
+    dx, dz = torch.empty_like(x), torch.empty_like(x)
+    dy = torch.empty_like(r_p)
+    it = ctypes.c_int()
+    rc = lib().nys_newton(h.h, m, n, NYS_F64, _ptr(_f64(A, "A")), A.stride(0), _ptr(_f64(x, "x")),
+                          _ptr(_f64(z, "z")), _ptr(_f64(D, "D")), float(delta), _ptr(_f64(r_d, "r_d")),
+                          _ptr(_f64(r_p, "r_p")), _ptr(_f64(r_xz, "r_xz")), ell, _ptr(_f64(U, "U")),
+                          U.shape[1], _ptr(_f64(lam, "lam")), float(eta), int(max_iter), int(forced),
+                          _ptr(dx), _ptr(dy), _ptr(dz), ctypes.byref(it))
+    h.check(rc)
+    return dx, dy, dz, it.value
+
+
+def nys_step_length(h: Handle, v, dv) -> float:
+    a = ctypes.c_double()
+    h.check(lib().nys_step_length(h.h, v.numel(), _ptr(_f64(v, "v")), _ptr(_f64(dv, "dv")),
+                                  ctypes.byref(a)))
+    return a.value
+
+
+def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check: bool = True,
+              lam0=None, zeta0=None, k0: int = 0, want_pmm: bool = False):
+    """Solve one QP.  CUDA tensors -> device problem; CPU tensors -> host
+    problem (the library stages the data; pin the tensors for fast copies).
+    lam0/zeta0/k0 resume from a saved state (rho/delta come from the handle's
+    options).  Returns (x, y, z, info); with want_pmm, info also holds the
+    final lam and zeta."""
+    m, n = A.shape
+    host = not A.is_cuda
+    dev = None if host else A.device
+    for t, nm in ((A, "A"), (b, "b"), (c, "c"), (q, "q"), (x0, "x0"), (y0, "y0"), (z0, "z0")):
+        _f64(t, nm, dev if not host else torch.device("cpu"))
+    mk = (lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True)) if host else \
+        (lambda k: torch.empty(k, dtype=torch.float64, device=dev))
+    x, y, z = mk(n), mk(m), mk(n)
+    lam, zeta = (mk(m), mk(n)) if want_pmm else (None, None)
+    for t, nm in ((lam0, "lam0"), (zeta0, "zeta0")):
+        if t is not None:
+            _f64(t, nm, dev if not host else torch.device("cpu"))
+    p = Problem(m=m, n=n, a_dtype=NYS_F64, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(),
+                c=c.data_ptr(), q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(),
+                z0=z0.data_ptr(), host=1 if host else 0,
+                lam0=lam0.data_ptr() if lam0 is not None else None,
+                zeta0=zeta0.data_ptr() if zeta0 is not None else None, k0=k0)
+    log = (ctypes.c_int * pcg_log_cap)()
+    r = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr(),
+               lam=lam.data_ptr() if lam is not None else None,
+               zeta=zeta.data_ptr() if zeta is not None else None,
+               pcg_log=log, pcg_log_cap=pcg_log_cap)
+    rc = lib().nys_solve(h.h, ctypes.byref(p), ctypes.byref(r))
+    if check:
+        h.check(rc)
+    info = {k: getattr(r, k) for k in ("status", "ipm_iters", "pcg_iters_total", "refine_steps",
+                                       "rel_primal", "rel_dual", "mu", "rel_gap", "rho", "delta",
+                                       "seconds")}
+    info["pcg_log"] = list(log[: r.pcg_log_len])
+    if want_pmm:
+        info["lam"], info["zeta"] = lam, zeta
+    return x, y, z, info

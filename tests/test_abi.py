@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/nys.h (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2404_14524_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "nys.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nys_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_header_declares_the_solver_api():
+    names = _declared()
+    for n in ("nys_create", "nys_solve", "nys_destroy", "nys_last_error", "nys_normal_matvec",
+              "nys_sketch", "nys_nystrom", "nys_pcg", "nys_precond_apply", "nys_step_length"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    from paper_2404_14524_gb300 import nys
+    assert sorted(nys.exported_symbols()) == _declared()
+    nys.lib()
+
+
+def test_struct_layouts_match_the_header(libpath):
+    """Sizes of the ctypes mirrors equal the C structs (compiled probe)."""
+    import subprocess
+    import tempfile
+    from paper_2404_14524_gb300 import nys
+    src = ('#include "nys.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+           'int main(){printf("%zu %zu %zu\\n", sizeof(nys_options), sizeof(nys_problem), sizeof(nys_result));return 0;}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "p")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(v) for v in out] == [ctypes.sizeof(nys.Options), ctypes.sizeof(nys.Problem),
+                                     ctypes.sizeof(nys.Result)]
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2404_14524_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "from oracle" not in txt and "import oracle" not in txt, f

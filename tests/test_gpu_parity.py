@@ -1,0 +1,361 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Element-by-element comparisons on the same seeded inputs, at sizes that span
+several tiles with ragged tails, plus the edge cases of each step.
+Tolerances: the FP64 form is compared at 1e-9 relative for whole-solve
+iterates (the stated target) and tighter for single steps, where only the
+summation order differs (bounds derived from n * 2^-53 growth).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import nys_oracle as O
+from paper_2404_14524_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nys():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_14524_gb300 import build
+    build.build()
+    from paper_2404_14524_gb300 import nys as N
+    N.lib()
+    return N
+
+
+DEV = torch.device("cuda", 0)
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def P(a):
+    """m x ell numpy panel -> (ell, m) tensor (column-major panel)."""
+    return T(np.asarray(a).T)
+
+
+def relerr(got, want):
+    got = got.detach().cpu().numpy() if isinstance(got, torch.Tensor) else got
+    d = np.linalg.norm(want)
+    return np.linalg.norm(got - want) / (d if d > 0 else 1.0)
+
+
+# ----------------------------------------------------------------- generators
+
+@pytest.mark.parametrize("m,ell,k", [(200, 20, 0), (517, 33, 5), (1, 1, 0)])
+def test_gaussian_matches_oracle(nys, m, ell, k):
+    h = nys.Handle(max(m, 2), 4, ell=ell)
+    got = nys.nys_gaussian(h, 12345, k, m, ell).cpu().numpy().T
+    want = O.gaussian_omega(12345, k, m, ell)
+    # same uniform bits; log/cos of two libraries may differ in the last ulps
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-14)
+
+
+# -------------------------------------------------------------- a1, a2
+
+@pytest.mark.parametrize("m,n", [(203, 517), (1, 1), (64, 1025), (777, 129)])
+def test_scaling_and_normal_matvec(nys, m, n):
+    rng = np.random.default_rng(m * 7 + n)
+    A = rng.standard_normal((m, n))
+    x, z, q = rng.uniform(0.1, 2, n), rng.uniform(0.01, 2, n), rng.uniform(0, 1, n)
+    q[::4] = 0
+    v = rng.standard_normal(m)
+    h = nys.Handle(m, n, ell=1)
+    D = nys.nys_scaling(h, T(x), T(z), T(q), 0.37)
+    Dw = O.scaling_D(x, z, q, 0.37)
+    assert relerr(D, Dw) <= 1e-15
+    out = nys.nys_normal_matvec(h, T(A), D, 1e-3, T(v))
+    want = O.normal_matvec(A, Dw, 1e-3, v)
+    tol = 4 * (m + n) * 2.0 ** -53 * np.linalg.norm(np.abs(A) @ (Dw * (np.abs(A).T @ np.abs(v))))
+    assert np.linalg.norm(out.cpu().numpy() - want) <= tol + 1e-300
+
+
+def test_normal_matvec_padded_leading_dimension(nys):
+    rng = np.random.default_rng(5)
+    m, n, lda = 130, 301, 320
+    Abig = rng.standard_normal((m, lda))
+    D, v = rng.uniform(0.1, 1, n), rng.standard_normal(m)
+    h = nys.Handle(m, n, ell=1)
+    At = T(Abig)[:, :n]                           # strided view, lda = 320
+    Dt, vt = T(D), T(v)                           # keep the tensors alive across the call
+    out = torch.empty(m, dtype=torch.float64, device=DEV)
+    lib = nys.lib()
+    rc = lib.nys_normal_matvec(h.h, m, n, 0, nys._ptr(At), lda, nys._ptr(Dt), 0.5, nys._ptr(vt),
+                               nys._ptr(out))
+    assert rc == 0
+    assert relerr(out, O.normal_matvec(Abig[:, :n], D, 0.5, v)) <= 1e-13
+
+
+# ------------------------------------------------------------------ a3, a4
+
+@pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (333, 700, 65), (70, 90, 70)])
+def test_sketch_matches_oracle(nys, m, n, ell):
+    rng = np.random.default_rng(m + n + ell)
+    A = rng.standard_normal((m, n)) / np.sqrt(n)
+    D = rng.uniform(0.05, 3, n)
+    Om = O.gaussian_omega(3, 1, m, ell)
+    h = nys.Handle(m, n, ell=ell)
+    Y = nys.nys_sketch(h, T(A), T(D), P(Om)).cpu().numpy().T
+    Yw = O.sketch(A, D, Om)
+    assert np.abs(Y - Yw).max() <= 1e-12 * np.abs(Yw).max()
+
+
+def _factor_pair(nys, m, n, ell, seed, rank=None, dscale=1.0):
+    rng = np.random.default_rng(seed)
+    if rank is None:
+        A = rng.standard_normal((m, n)) * (np.arange(1, m + 1) ** -1.0)[:, None]
+    else:
+        A = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n)) / np.sqrt(n)
+    D = rng.uniform(0.1, 3, n) * dscale
+    Om = O.gaussian_omega(seed, 0, m, ell)
+    Y = O.sketch(A, D, Om)
+    Fw = O.nystrom_from_sketch(Y, Om)
+    h = nys.Handle(m, n, ell=ell)
+    U, lam, nu = nys.nys_nystrom(h, P(Y), P(Om))
+    return h, A, D, Om, Fw, U.cpu().numpy().T, lam.cpu().numpy(), nu
+
+
+@pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (301, 450, 47), (64, 64, 64), (5, 9, 1)])
+def test_nystrom_factor_matches_oracle(nys, m, n, ell):
+    h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, m, n, ell, seed=m + ell)
+    assert nu == Fw.nu
+    assert np.all(np.diff(lam) <= 0) and np.all(lam >= 0)
+    assert np.allclose(lam, Fw.lam, rtol=1e-10, atol=1e-12 * Fw.lam[0])
+    assert np.abs(U.T @ U - np.eye(ell)).max() < 1e-12
+    Nh, Nhw = U @ np.diag(lam) @ U.T, Fw.U @ np.diag(Fw.lam) @ Fw.U.T
+    assert np.linalg.norm(Nh - Nhw, 2) <= 1e-10 * np.linalg.norm(Nhw, 2)
+
+
+def test_nystrom_exact_for_low_rank(nys):
+    h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, 120, 300, 12, seed=9, rank=6)
+    N = A @ (D[:, None] * A.T)
+    assert np.linalg.norm(U @ np.diag(lam) @ U.T - N, 2) <= 1e-9 * np.linalg.norm(N, 2)
+
+
+def test_nystrom_ill_conditioned_scaling(nys):
+    """D spanning 12 orders of magnitude (late IPM iterations)."""
+    rng = np.random.default_rng(4)
+    m, n, ell = 150, 400, 30
+    A = rng.standard_normal((m, n)) / np.sqrt(n)
+    D = 10.0 ** rng.uniform(-6, 6, n)
+    Om = O.gaussian_omega(4, 2, m, ell)
+    Y = O.sketch(A, D, Om)
+    Fw = O.nystrom_from_sketch(Y, Om)
+    h = nys.Handle(m, n, ell=ell)
+    U, lam, nu = nys.nys_nystrom(h, P(Y), P(Om))
+    U, lam = U.cpu().numpy().T, lam.cpu().numpy()
+    assert np.allclose(lam, Fw.lam, rtol=1e-8, atol=1e-13 * Fw.lam[0])
+    delta = 1e-6
+    r = rng.standard_normal(m)
+    got = nys.nys_precond_apply(h, P(U), T(lam), delta, T(r))
+    want = O.precond_inv_apply(Fw, delta, r)
+    assert relerr(got, want) <= 1e-8
+
+
+# -------------------------------------------------------------------- a6, a5
+
+@pytest.mark.parametrize("m,ell", [(200, 20), (513, 1), (1000, 100)])
+def test_precond_apply_matches_oracle(nys, m, ell):
+    rng = np.random.default_rng(m)
+    Uq, _ = np.linalg.qr(rng.standard_normal((m, ell)))
+    lam = np.sort(rng.uniform(0, 5, ell))[::-1].copy()
+    lam[-1] = 0.0
+    F = O.NystromFactor(U=Uq, lam=lam, nu=0.0)
+    r = rng.standard_normal(m)
+    h = nys.Handle(m, 4, ell=ell)
+    for delta in (1e-9, 1e-2, 4.0):
+        got = nys.nys_precond_apply(h, P(Uq), T(lam), delta, T(r))
+        assert relerr(got, O.precond_inv_apply(F, delta, r)) <= 1e-13
+
+
+@pytest.mark.parametrize("m,n,ell,delta", [(200, 500, 20, 1e-3), (257, 611, 31, 1e-6)])
+def test_pcg_matches_oracle(nys, m, n, ell, delta):
+    h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, m, n, ell, seed=11 + m)
+    rng = np.random.default_rng(1)
+    xi = rng.standard_normal(m)
+    eta = 1e-8
+    want = O.pcg(lambda v: O.normal_matvec(A, D, delta, v), lambda v: O.precond_inv_apply(Fw, delta, v),
+                 xi, eta, 1000)
+    dy, it, res, rc = nys.nys_pcg(h, T(A), T(D), delta, P(U), T(lam), T(xi), eta, 1000)
+    assert it == want.iters and rc == 0
+    assert relerr(dy, want.x) <= 1e-9
+    # forced count and a zero right-hand side
+    dy, it, res, rc = nys.nys_pcg(h, T(A), T(D), delta, P(U), T(lam), T(xi), eta, 1000, forced=3)
+    w3 = O.pcg(lambda v: O.normal_matvec(A, D, delta, v), lambda v: O.precond_inv_apply(Fw, delta, v),
+               xi, eta, 1000, forced_iters=3)
+    assert it == 3 and relerr(dy, w3.x) <= 1e-11
+    dy, it, res, rc = nys.nys_pcg(h, T(A), T(D), delta, P(U), T(lam), T(np.zeros(m)), eta, 1000)
+    assert it == 0 and float(dy.abs().max()) == 0.0
+
+
+def test_pcg_max_iter_warning(nys):
+    h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, 150, 300, 5, seed=3)
+    xi = np.random.default_rng(2).standard_normal(150)
+    dy, it, res, rc = nys.nys_pcg(h, T(A), T(D), 1e-9, P(U), T(lam), T(xi), 1e-14, 4)
+    assert it == 4 and rc == nys.NYS_WARN_PCG_MAXITER
+
+
+# ----------------------------------------------------------------- a7, a8
+
+def test_newton_direction_matches_oracle(nys):
+    rng = np.random.default_rng(8)
+    m, n, ell = 150, 420, 15
+    A = rng.standard_normal((m, n)) / np.sqrt(n)
+    x, z = rng.uniform(0.1, 2, n), rng.uniform(0.1, 2, n)
+    q = rng.uniform(0, 1, n)
+    rho, delta = 0.2, 0.05
+    D = O.scaling_D(x, z, q, rho)
+    Om = O.gaussian_omega(1, 0, m, ell)
+    F = O.nystrom(A, D, Om)
+    r_d, r_p, r_xz = rng.standard_normal(n), rng.standard_normal(m), -x * z
+    want = O.newton_direction(A, x, z, D, delta, r_d, r_p, r_xz, F, 1e-10, 500)
+    h = nys.Handle(m, n, ell=ell)
+    dx, dy, dz, it = nys.nys_newton(h, T(A), T(x), T(z), T(D), delta, T(r_d), T(r_p), T(r_xz),
+                                    P(F.U), T(F.lam), 1e-10, 500)
+    assert it == want.pcg_iters
+    for g, w in ((dx, want.dx), (dy, want.dy), (dz, want.dz)):
+        assert relerr(g, w) <= 1e-10
+
+
+def test_step_length_bit_exact(nys):
+    rng = np.random.default_rng(9)
+    h = nys.Handle(4, 5000, ell=1)
+    for n in (1, 7, 5000):
+        v = rng.uniform(0.01, 2, n)
+        dv = rng.standard_normal(n) * 3
+        assert nys.nys_step_length(h, T(v), T(dv)) == O.step_length(v, dv)
+    v = np.ones(10)
+    assert nys.nys_step_length(h, T(v), T(np.ones(10))) == 0.995     # no negative component
+
+
+# ------------------------------------------------------------------ whole solve
+
+def _omega_sensitivity(qp, opt, state, k, lam, zeta):
+    """How far one oracle IPM step moves when Omega_k is perturbed by 2e-16
+    relative: the rounding-level noise floor of that step (late IPM steps run
+    many CG iterations on ill-conditioned systems, which amplify rounding)."""
+    orig = O.gaussian_omega
+
+    def pert(seed, kk, m, ell):
+        om = orig(seed, kk, m, ell)
+        return om * (1 + 2e-16 * np.sign(np.sin(np.arange(om.size))).reshape(om.shape))
+    x, y, z = state
+    a = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, lam0=lam, zeta0=zeta, k0=k)
+    O.gaussian_omega = pert
+    try:
+        b = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, lam0=lam, zeta0=zeta, k0=k)
+    finally:
+        O.gaussian_omega = orig
+    return max(relerr(u, v) for u, v in ((a.x, b.x), (a.y, b.y), (a.z, b.z)))
+
+
+@pytest.fixture(scope="module")
+def small_run():
+    qp = synth.workload_small()
+    ref = O.solve_qp(qp, O.Options(tol=1e-6, ell=20, seed=7), record=True)
+    return qp, ref
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 9, 13, 18, 22, 26, 27])
+def test_single_ipm_step_matches_oracle(nys, small_run, k):
+    """One IPM iteration (sketch, core, two PCG solves, steps, PEU) resumed on
+    the GPU from the oracle's state k, with the oracle's PCG counts: the next
+    iterate must agree to 1e-9 relative, or to 100x the oracle's own response
+    to a 2e-16 perturbation of Omega_k where that floor is higher."""
+    qp, ref = small_run
+    t = ref.trace[k]
+    x, y, z, lam, zeta = t.state
+    forced = [t.pcg_pred, t.pcg_corr]
+    opt = O.Options(tol=1e-6, ell=20, seed=7, rho0=t.rho, delta0=t.delta, forced_ipm=1, forced_pcg=forced)
+    nxt = ref.trace[k + 1] if k + 1 < len(ref.trace) else None
+    want = nxt.state[:3] if nxt is not None else (ref.x, ref.y, ref.z)
+    floor = _omega_sensitivity(qp, opt, (x, y, z), k, lam, zeta)
+    tol = max(1e-9, 100 * floor)
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=forced, forced_ipm=1,
+                   rho0=t.rho, delta0=t.delta)
+    gx, gy, gz, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(x), T(y), T(z),
+                                     lam0=T(lam), zeta0=T(zeta), k0=k)
+    errs = [relerr(g, w) for g, w in ((gx, want[0]), (gy, want[1]), (gz, want[2]))]
+    print(f"k={k} errs={errs} floor={floor:.2e}")
+    assert max(errs) <= tol
+    if nxt is not None:
+        assert abs(info["rho"] - nxt.rho) <= 1e-9 * nxt.rho
+        assert abs(info["delta"] - nxt.delta) <= 1e-9 * nxt.delta
+
+
+def test_small_workload_solution_matches_oracle(nys, small_run):
+    """Whole m=200, n=500 solve with the oracle's PCG and IPM counts: same KKT
+    quality, and the final iterates agree far below the 1e-6 tolerance (the
+    oracle itself moves ~1e-7 under a 2e-16 perturbation of Omega)."""
+    qp, ref = small_run
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=ref.pcg_iters, forced_ipm=ref.ipm_iters)
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    assert info["ipm_iters"] == ref.ipm_iters and info["pcg_log"] == ref.pcg_iters
+    for g, w in ((x, ref.x), (y, ref.y), (z, ref.z)):
+        assert relerr(g, w) <= 1e-5
+    assert info["rel_primal"] <= 1e-6 and info["rel_dual"] <= 1e-6 and info["mu"] <= 1e-6
+
+
+def test_free_running_solve_meets_kkt(nys):
+    """Without forced counts the GPU decides its own PCG exits and stops by its
+    own KKT test; it must converge to the same point within the tolerance."""
+    qp = synth.workload_small(seed=77)
+    ref = O.solve_qp(qp, O.Options(tol=1e-8, ell=20, seed=3))
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-8, seed=3)
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    assert info["status"] == 0
+    rp, rd, mu = O.kkt_measures(qp.A, qp.b, qp.c, qp.q, *(t.cpu().numpy() for t in (x, y, z)))
+    assert rp <= 1e-8 and rd <= 1e-8 and mu <= 1e-8
+    assert relerr(x, ref.x) <= 1e-5
+
+
+def test_host_buffers_give_identical_results(nys):
+    qp = synth.workload_small(seed=5)
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=1)
+    dev = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    cpu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    host = nys.nys_solve(h, cpu(qp.A), cpu(qp.b), cpu(qp.c), cpu(qp.q), cpu(qp.x0), cpu(qp.y0), cpu(qp.z0))
+    for a, b in zip(dev[:3], host[:3]):
+        assert torch.equal(a.cpu(), b)
+
+
+def test_tiny_and_degenerate_problems(nys):
+    """m = 1 with ell = 1, and an LP (q = 0), against hand-derived KKT points."""
+    h = nys.Handle(1, 3, ell=1, tol=1e-9)
+    A, b = np.array([[1.0, 1.0, 1.0]]), np.array([1.0])
+    c, q = np.array([1.0, 2.0, 3.0]), np.zeros(3)
+    x, y, z, info = nys.nys_solve(h, T(A), T(b), T(c), T(q), T(np.ones(3)), T(np.zeros(1)), T(np.ones(3)))
+    assert info["status"] == 0
+    assert np.allclose(x.cpu().numpy(), [1, 0, 0], atol=1e-7) and abs(float(y[0]) - 1.0) < 1e-6
+
+
+def test_bad_arguments_are_rejected(nys):
+    h = nys.Handle(10, 20, ell=5)
+    lib = nys.lib()
+    out = torch.empty(10, dtype=torch.float64, device=DEV)
+    A = torch.zeros(10, 20, dtype=torch.float64, device=DEV)
+    # m larger than the handle, wrong dtype, lda < n
+    assert lib.nys_normal_matvec(h.h, 11, 20, 0, nys._ptr(A), 20, nys._ptr(out), 0.0, nys._ptr(out), nys._ptr(A)) == -1
+    assert lib.nys_normal_matvec(h.h, 10, 20, 2, nys._ptr(A), 20, nys._ptr(out), 0.0, nys._ptr(out), nys._ptr(A)) == -1
+    assert lib.nys_normal_matvec(h.h, 10, 20, 0, nys._ptr(A), 19, nys._ptr(out), 0.0, nys._ptr(out), nys._ptr(A)) == -1
+    assert "bad argument" in nys.nys_last_error(h)
+
+
+def test_core_breakdown_is_reported_not_trapped(nys):
+    """Omega = 0 makes Omega^T Y_nu singular: the Cholesky must report a
+    breakdown status (no trap) and the handle must stay usable."""
+    m, ell = 50, 5
+    h = nys.Handle(m, 10, ell=ell)
+    Y = P(np.random.default_rng(0).standard_normal((m, ell)))
+    Z = torch.zeros_like(Y)
+    with pytest.raises(nys.NysError) as e:
+        nys.nys_nystrom(h, Y, Z)
+    assert e.value.code == nys.NYS_ERR_CORE_BREAKDOWN
+    # still usable
+    out = nys.nys_precond_apply(h, P(np.eye(m)[:, :ell]), T(np.ones(ell)), 1.0, T(np.ones(m)))
+    assert torch.isfinite(out).all()
