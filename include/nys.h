@@ -199,6 +199,16 @@ int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long
                double eta, int max_iter, int forced_iters,
                double* dx, double* dy, double* dz, int* iters);
 
+/* C = A B^T on the tcgen05 tensor cores, BF16 inputs, FP32 accumulation: the
+ * two products of the sketch (Algorithm 1, second step) in the precision form
+ * are of this shape (A^T Omega with A^T stored row-major, and A T').
+ * A: M x K, B: N x K, both BF16 row-major with K contiguous, leading
+ * dimensions multiples of 8 elements, 16-byte aligned; C: FP32 column-major
+ * M x N, ldc >= M.  N <= 512.  Device pointers.  The split-K partial sums use
+ * the handle's workspace: NYS_ERR_ARG if they do not fit (M * N * splits). */
+int nys_gemm_bf16(nys_handle h, int M, int N, int K, const void* A, long long lda, const void* B,
+                  long long ldb, float* C, long long ldc);
+
 /* Fraction-to-boundary step (Eq. stepsize-p / stepsize-d):
  * *alpha = 0.995 min{1, min over dv_i < 0 of -v_i / dv_i}.
  * v, dv: device length n; *alpha: host. */

@@ -87,8 +87,9 @@ template <bool kVec>
 __global__ void __launch_bounds__(kNT) k_av(int m, int n, const double* __restrict__ A, long long lda,
                                             const double* __restrict__ t, double beta,
                                             const double* __restrict__ v, double* __restrict__ out,
-                                            const int* __restrict__ skip) {
+                                            const int* __restrict__ skip, const double* __restrict__ beta_dev) {
   if (skip && *skip) return;
+  if (beta_dev) beta = *beta_dev;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (row >= m) return;
@@ -156,13 +157,13 @@ cudaError_t gemv_t_f64(cudaStream_t st, int m, int n, const double* A, long long
 
 cudaError_t gemv_n_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
                        const double* t, double beta, const double* v, double* out,
-                       const int* skip) {
+                       const int* skip, const double* beta_dev) {
   if (m <= 0) return cudaSuccess;
   const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) &&
                    ((reinterpret_cast<uintptr_t>(t) & 15u) == 0);
   const int blocks = (m + kWarps - 1) / kWarps;
-  if (vec) { count_launches(1); k_av<true><<<blocks, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip); }
-  else { count_launches(1); k_av<false><<<blocks, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip); }
+  if (vec) { count_launches(1); k_av<true><<<blocks, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip, beta_dev); }
+  else { count_launches(1); k_av<false><<<blocks, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip, beta_dev); }
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // Every launcher issues its kernels on `st` and returns a cudaError_t of the
 // launch (kernel-side failures are reported through the device error word).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -21,6 +22,7 @@ enum ScalarD : int {
   SD_ETA2,        // eta^2 (relative tolerance squared)
   SD_FROB2,       // ||Y||_F^2 of the sketch
   SD_NU,          // nu of Algorithm 1
+  SD_DELTA,       // delta of the system being solved by PCG
   SD_RED0,        // generic reduction outputs
   SD_RED1,
   SD_RED2,
@@ -51,10 +53,11 @@ struct RedBuf {
 cudaError_t gemv_t_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
                        const double* v, const double* D, double* t, double* split_buf,
                        size_t split_cap, const int* skip = nullptr);
-// out[i] = sum_j A[i, j] t[j] + beta * v[i]   (v may be nullptr when beta == 0)
+// out[i] = sum_j A[i, j] t[j] + beta * v[i]   (v may be nullptr when beta == 0);
+// when beta_dev is given, beta is read from device memory instead.
 cudaError_t gemv_n_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
                        const double* t, double beta, const double* v, double* out,
-                       const int* skip = nullptr);
+                       const int* skip = nullptr, const double* beta_dev = nullptr);
 // Rows of split-reduction scratch that gemv_t_f64 needs for an m x n matrix.
 size_t gemv_t_split_elems(int m, int n);
 
@@ -95,6 +98,38 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
                              int ld, double* U, double* lam, double* sd, int* si, RedBuf red,
                              CoreWork cw, int num_sms);
 
+// ---------------------------------------------------------------- precision-form GEMVs
+// out[r] = scale[r] * sum_c A[r, c] x[c] + beta v[r]; A BF16 (a_bf16) or FP32
+// row-major, x/scale FP32, FP32 accumulation; out FP64 (out_f64) or FP32.
+cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_bf16, const void* A, long long lda,
+                         const float* x, const float* scale, double beta, const double* v, void* out,
+                         int out_f64, const int* skip = nullptr, const double* beta_dev = nullptr);
+// FP32 A times x = xh + xl with float-float accumulation, FP64 out.
+cudaError_t gemv_rows_ff(cudaStream_t st, int rows, int cols, const float* A, long long lda, const float* xh,
+                         const float* xl, const double* scale, double beta, const double* v, double* out);
+// hi/lo FP32 split of scale .* x, zero padded to npad
+cudaError_t split_ff(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* hi, float* lo);
+cudaError_t to_f32(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* y,
+                   const int* skip = nullptr);
+// BF16 copy (dst, ldd), BF16 transpose (dstT, ldt) and FP32 transpose (dstTf,
+// ldtf) of a row-major FP32/FP64 matrix; any output may be null; padding zeroed.
+cudaError_t convert_transpose(cudaStream_t st, int rows, int cols, int src_f64, const void* src, long long lds,
+                              __nv_bfloat16* dst, long long ldd, __nv_bfloat16* dstT, long long ldt,
+                              float* dstTf, long long ldtf);
+
+// ---------------------------------------------------------------- tcgen05 BF16 GEMM
+// part[z][c][r] = sum_{k in split z} A[r, k] B[c, k]; A: M x K, B: N x K, both
+// BF16 row-major (K contiguous, leading dimensions multiples of 8), N <= 512.
+// *S_out receives the number of K splits used (part must hold S*Npad*M floats,
+// Npad = N rounded up to 16).
+size_t umma_part_elems(int M, int N, int K, int num_sms);
+cudaError_t umma_gemm_bf16(cudaStream_t st, int M, int N, int K, const void* A, long long lda,
+                           const void* B, long long ldb, float* part, size_t part_cap, int num_sms,
+                           int* S_out, int* err);
+// out[c*ldo + r] = sum_z part[z][c][r]: mode 0 FP32 out; mode 1 scaled by D[r], BF16 out.
+cudaError_t umma_reduce(cudaStream_t st, int M, int N, int S, const float* part, int mode,
+                        const double* D, void* out, long long ldo);
+
 // ---------------------------------------------------------------- PCG / P^{-1}
 struct PcgWork {
   double *x, *r, *z, *p, *w;  // m each
@@ -112,10 +147,28 @@ cudaError_t precond_apply_f64(cudaStream_t st, int m, int ell, const double* U, 
 cudaError_t pcg_setup_f64(cudaStream_t st, int m, int ell, const double* U, int ld,
                           const double* lam, double delta, const double* xi, double eta,
                           int max_iter, int forced, PcgWork w, double* sd, int* si, RedBuf red);
-// Issue one predicated PCG iteration (no-op once SI_DONE is set).
+// Issue one predicated PCG iteration (no-op once SI_DONE is set).  delta is
+// read from sd[SD_DELTA] (written by the setup), so a captured iteration
+// stays valid across solves.
 cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
-                              const double* D, double delta, int ell, const double* U, int ld,
+                              const double* D, int ell, const double* U, int ld,
                               PcgWork w, double* sd, int* si, RedBuf red);
+// Reduced-precision operator (N + delta I) p for the precision form: A and
+// A^T stored row-major in BF16 (bf16 = 1) or FP32, D in FP32; scratch xf
+// (ld_mpad floats, zero padded) and tf (n floats).
+struct LpOperator {
+  int bf16;
+  const void* A;  long long lda;    // m x n
+  const void* AT; long long ldat;   // n x m
+  const float* Df;
+  float* xf;
+  float* tf;
+  int ld_mpad;
+};
+cudaError_t pcg_iteration_lp(cudaStream_t st, int m, int n, const LpOperator& op, int ell,
+                             const double* U, int ld, PcgWork w, double* sd, int* si, RedBuf red);
+// Body-graph tail of a conditional while node: keep looping while !SI_DONE.
+cudaError_t pcg_loop_condition(cudaStream_t st, cudaGraphConditionalHandle cond, const int* si);
 
 // ---------------------------------------------------------------- IPM vectors
 // Residuals at the top of an IPM iteration (Eq. predictor-RHS, I = all):
@@ -153,6 +206,12 @@ cudaError_t add_dirs_f64(cudaStream_t st, int m, int n, const double* dxp, const
 // x += ap dx; z += ad dz (n);  y += ad dy (m)
 cudaError_t ipm_update_f64(cudaStream_t st, int m, int n, double ap, double ad, const double* dx,
                            const double* dy, const double* dz, double* x, double* y, double* z);
+// out = a x + b y
+cudaError_t axpby_f64(cudaStream_t st, int len, double a, const double* x, double b, const double* y, double* out);
+// P (m x ell, column-major, FP64) rounded to BF16 in place; the BF16 copy goes
+// to Pb with leading dimension ldb (rows of the transposed panel).
+cudaError_t round_panel_bf16(cudaStream_t st, int m, int ell, double* P, int ld, __nv_bfloat16* Pb, int ldb);
+cudaError_t panel_f32_to_f64(cudaStream_t st, int m, int ell, const float* src, int lds, double* dst, int ldd);
 // out = a^T b (device scalar)
 cudaError_t dot_f64(cudaStream_t st, int len, const double* a, const double* b, double* out,
                     RedBuf red);

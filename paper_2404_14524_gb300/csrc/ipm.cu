@@ -160,7 +160,55 @@ __global__ void __launch_bounds__(kNT) k_objective(int m, int n, const double* _
     for (int k = 0; k < 4; ++k) out[k] = tot[k];
 }
 
+// out = a x + b y
+__global__ void k_axpby(int len, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out) {
+  const int j = blockIdx.x * kNT + threadIdx.x;
+  if (j < len) out[j] = fma(a, x[j], b * y[j]);
+}
+
+// Round a column-major FP64 panel to BF16 (rows of the transposed BF16 copy)
+// and write the rounded values back, so both views hold the same numbers.
+__global__ void k_round_panel_bf16(int m, int ell, double* __restrict__ P, int ld, __nv_bfloat16* __restrict__ Pb,
+                                   int ldb) {
+  const long long idx = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (idx >= (long long)m * ell) return;
+  const int i = (int)(idx % m), c = (int)(idx / m);
+  const __nv_bfloat16 v = __float2bfloat16_rn((float)P[(size_t)c * ld + i]);
+  Pb[(size_t)c * ldb + i] = v;
+  P[(size_t)c * ld + i] = (double)__bfloat162float(v);
+}
+
+__global__ void k_panel_f32_to_f64(int m, int ell, const float* __restrict__ src, int lds, double* __restrict__ dst,
+                                   int ldd) {
+  const long long idx = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (idx >= (long long)m * ell) return;
+  const int i = (int)(idx % m), c = (int)(idx / m);
+  dst[(size_t)c * ldd + i] = (double)src[(size_t)c * lds + i];
+}
+
 }  // namespace
+
+cudaError_t axpby_f64(cudaStream_t st, int len, double a, const double* x, double b, const double* y, double* out) {
+  if (len <= 0) return cudaSuccess;
+  count_launches(1);
+  k_axpby<<<(len + kNT - 1) / kNT, kNT, 0, st>>>(len, a, x, b, y, out);
+  return cudaGetLastError();
+}
+
+cudaError_t round_panel_bf16(cudaStream_t st, int m, int ell, double* P, int ld, __nv_bfloat16* Pb, int ldb) {
+  const long long total = (long long)m * ell;
+  count_launches(1);
+  k_round_panel_bf16<<<(unsigned)((total + kNT - 1) / kNT), kNT, 0, st>>>(m, ell, P, ld, Pb, ldb);
+  return cudaGetLastError();
+}
+
+cudaError_t panel_f32_to_f64(cudaStream_t st, int m, int ell, const float* src, int lds, double* dst, int ldd) {
+  const long long total = (long long)m * ell;
+  count_launches(1);
+  k_panel_f32_to_f64<<<(unsigned)((total + kNT - 1) / kNT), kNT, 0, st>>>(m, ell, src, lds, dst, ldd);
+  return cudaGetLastError();
+}
 
 cudaError_t ipm_residuals_f64(cudaStream_t st, int m, int n, const double* b, const double* c,
                               const double* q, const double* x, const double* y,

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kNT) k_pcg_setup1(int m, int ell, const double
       si[SI_ITERS] = 0;
       si[SI_FORCED] = forced;
       si[SI_MAXIT] = max_iter;
+      sd[SD_DELTA] = delta;
       const int limit = forced >= 0 ? forced : max_iter;
       si[SI_DONE] = (tot[0] == 0.0 || limit <= 0) ? 1 : 0;
       if (!isfinite(tot[0])) { si[SI_DONE] = 1; set_error(si + SI_ERR, kErrNumeric); }
@@ -216,12 +217,22 @@ __global__ void __launch_bounds__(kNT) k_ut_r(int m, int ell, const double* __re
   }
 }
 
+__global__ void k_pcg_cond(cudaGraphConditionalHandle cond, const int* si) {
+  cudaGraphSetConditional(cond, si[SI_DONE] ? 0u : 1u);
+}
+
 int vec_blocks(int m) {
   int b = (m + kNT - 1) / kNT;
   return b > 2 * 152 ? 2 * 152 : (b < 1 ? 1 : b);
 }
 
 }  // namespace
+
+cudaError_t pcg_loop_condition(cudaStream_t st, cudaGraphConditionalHandle cond, const int* si) {
+  count_launches(1);
+  k_pcg_cond<<<1, 1, 0, st>>>(cond, si);
+  return cudaGetLastError();
+}
 
 cudaError_t precond_apply_f64(cudaStream_t st, int m, int ell, const double* U, int ld,
                               const double* lam, double delta, const double* r, double* out,
@@ -252,14 +263,9 @@ cudaError_t pcg_setup_f64(cudaStream_t st, int m, int ell, const double* U, int 
   return cudaGetLastError();
 }
 
-cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
-                              const double* D, double delta, int ell, const double* U, int ld,
-                              PcgWork w, double* sd, int* si, RedBuf red) {
-  const int* done = si + SI_DONE;
-  cudaError_t e = gemv_t_f64(st, m, n, A, lda, w.p, D, w.t, w.split_buf, w.split_cap, done);
-  if (e != cudaSuccess) return e;
-  e = gemv_n_f64(st, m, n, A, lda, w.t, delta, w.p, w.w, done);
-  if (e != cudaSuccess) return e;
+// CG vector updates of one iteration after w = (N + delta I) p is available.
+static cudaError_t pcg_tail(cudaStream_t st, int m, int ell, const double* U, int ld, PcgWork w,
+                            double* sd, int* si, RedBuf red) {
   count_launches(1);
   k_pcg_alpha<<<vec_blocks(m), kNT, 0, st>>>(m, w.p, w.w, sd, si, red.part, red.cnt + 3);
   const int rows = band_rows(m);
@@ -273,6 +279,30 @@ cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, lo
   count_launches(1);
   k_pcg_p<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, w.z, w.p, sd, si, 0);
   return cudaGetLastError();
+}
+
+cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
+                              const double* D, int ell, const double* U, int ld,
+                              PcgWork w, double* sd, int* si, RedBuf red) {
+  const int* done = si + SI_DONE;
+  cudaError_t e = gemv_t_f64(st, m, n, A, lda, w.p, D, w.t, w.split_buf, w.split_cap, done);
+  if (e != cudaSuccess) return e;
+  e = gemv_n_f64(st, m, n, A, lda, w.t, 1.0, w.p, w.w, done, sd + SD_DELTA);
+  if (e != cudaSuccess) return e;
+  return pcg_tail(st, m, ell, U, ld, w, sd, si, red);
+}
+
+cudaError_t pcg_iteration_lp(cudaStream_t st, int m, int n, const LpOperator& op, int ell,
+                             const double* U, int ld, PcgWork w, double* sd, int* si, RedBuf red) {
+  const int* done = si + SI_DONE;
+  // pf = FP32(p);  tf = Df .* (A^T pf);  w = A tf + delta p
+  cudaError_t e = to_f32(st, m, op.ld_mpad, w.p, nullptr, op.xf, done);
+  if (e != cudaSuccess) return e;
+  e = gemv_rows_lp(st, n, m, op.bf16, op.AT, op.ldat, op.xf, op.Df, 0.0, nullptr, op.tf, 0, done);
+  if (e != cudaSuccess) return e;
+  e = gemv_rows_lp(st, m, n, op.bf16, op.A, op.lda, op.tf, nullptr, 1.0, w.p, w.w, 1, done, sd + SD_DELTA);
+  if (e != cudaSuccess) return e;
+  return pcg_tail(st, m, ell, U, ld, w, sd, si, red);
 }
 
 }  // namespace nys

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -57,6 +58,30 @@ struct nys_solver {
   // device staging for problems given in host memory
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // PCG as one graph launch: a conditional while node whose body is one
+  // predicated iteration (rebuilt when the operator's pointers change)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t pcg_graph = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  const void* gk_A = nullptr;
+  const double *gk_D = nullptr, *gk_U = nullptr;
+  long long gk_lda = 0;
+  int gk_m = 0, gk_n = 0, gk_ell = 0, gk_ld = 0;
+  unsigned g_kernels_per_iter = 0;
+  bool use_graphs = true;
+  int gk_op = -1;            // graph key: operator kind
+  double* pcg_x = nullptr;   // PCG solution buffer (copied out after each solve)
+  // precision form (precision_mode 1): A is FP32 (the problem definition);
+  // BF16 copies of A and A^T feed the inner PCG and the tensor-core sketch,
+  // an FP32 copy of A^T the refinement residual.
+  void* lp_arena = nullptr;
+  size_t lp_bytes = 0;
+  __nv_bfloat16 *Ab = nullptr, *AbT = nullptr, *Omb = nullptr, *Tb = nullptr;
+  float *AfT = nullptr, *upart = nullptr, *Y32 = nullptr, *xf = nullptr, *tf = nullptr, *Df = nullptr;
+  float *fh = nullptr, *fl = nullptr;
+  size_t upart_cap = 0;
+  long long ld_b = 0, ld_bt = 0, ld_ft = 0, ld_om = 0, ld_tb = 0, ld_ff = 0;
+  double *nd_m = nullptr, *u_n = nullptr, *rr = nullptr, *dyacc = nullptr, *ecorr = nullptr;
 };
 
 namespace {
@@ -120,6 +145,7 @@ size_t carve(nys_solver* h, char* base) {
   h->cw.sweep_flags = c.take<int>(CoreWork::kMaxSweeps);
   h->cw.split_buf = h->split_buf;
   h->cw.split_cap = h->split_cap;
+  h->pcg_x = c.take<double>(M);
   h->pw.r = c.take<double>(M);
   h->pw.z = c.take<double>(M);
   h->pw.p = c.take<double>(M);
@@ -153,6 +179,37 @@ size_t carve(nys_solver* h, char* base) {
   return c.off;
 }
 
+size_t carve_lp(nys_solver* h, char* base) {
+  Carver c{base};
+  const size_t M = h->max_m, N = h->max_n, L = h->ell_cap;
+  h->ld_b = (long long)align_up(M > 0 ? N : 0, 8);
+  h->ld_bt = (long long)align_up(M, 8);
+  h->ld_ft = (long long)align_up(M, 4);
+  h->ld_om = (long long)align_up(M, 8);
+  h->ld_tb = (long long)align_up(N, 8);
+  h->ld_ff = (long long)std::max(align_up(M, 8), align_up(N, 8));
+  h->Ab = c.take<__nv_bfloat16>(M * (size_t)h->ld_b);
+  h->AbT = c.take<__nv_bfloat16>(N * (size_t)h->ld_bt);
+  h->AfT = c.take<float>(N * (size_t)h->ld_ft);
+  h->Omb = c.take<__nv_bfloat16>(L * (size_t)h->ld_om);
+  h->Tb = c.take<__nv_bfloat16>(L * (size_t)h->ld_tb);
+  h->upart_cap = std::max(umma_part_elems((int)N, (int)L, (int)M, h->num_sms),
+                          umma_part_elems((int)M, (int)L, (int)N, h->num_sms));
+  h->upart = c.take<float>(h->upart_cap);
+  h->Y32 = c.take<float>((size_t)h->ld * L);
+  h->xf = c.take<float>(h->ld_ff);
+  h->tf = c.take<float>(h->ld_ff);
+  h->Df = c.take<float>(h->ld_ff);
+  h->fh = c.take<float>(h->ld_ff);
+  h->fl = c.take<float>(h->ld_ff);
+  h->nd_m = c.take<double>(M);
+  h->u_n = c.take<double>(N);
+  h->rr = c.take<double>(M);
+  h->dyacc = c.take<double>(M);
+  h->ecorr = c.take<double>(M);
+  return c.off;
+}
+
 int check_err(nys_solver* h) {
   const int e = h->h_si[SI_ERR];
   if (e == 0) return NYS_OK;
@@ -174,24 +231,122 @@ int sync_scalars(nys_solver* h, int n_red) {
 
 int valid_ptr(const void* p) { return p != nullptr; }
 
-// Run PCG on (A D A^T + delta I) dy = xi; dy is written into `out`.
-int run_pcg(nys_solver* h, int m, int n, const double* A, long long lda, const double* D,
-            double delta, int ell, const double* U, int ld, const double* lamh, const double* xi,
-            double* out, double eta, int max_iter, int forced, int* iters) {
+int sync_scalars_at(nys_solver* h, int off, int n_red) {
+  CK(cudaMemcpyAsync(h->h_si, h->si, sizeof(int) * SI_COUNT, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_red + off, h->red_out + off, sizeof(double) * n_red, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return check_err(h);
+}
+
+void drop_pcg_graph(nys_solver* h) {
+  if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
+  if (h->pcg_graph) cudaGraphDestroy(h->pcg_graph);
+  h->pcg_exec = nullptr;
+  h->pcg_graph = nullptr;
+  h->gk_A = nullptr;
+}
+
+// The operator (N + delta I) p used inside PCG: FP64 A (kind 0), or the
+// precision form's BF16 (kind 1) / FP32 (kind 2) row-major copies.
+struct OpSpec {
+  int kind;
+  const double* A;      // kind 0
+  long long lda;
+  const double* D;      // kind 0
+  LpOperator lp;        // kinds 1, 2
+  const void* key() const { return kind == 0 ? (const void*)A : lp.A; }
+};
+
+cudaError_t issue_pcg_iteration(nys_solver* h, cudaStream_t st, int m, int n, const OpSpec& op, int ell,
+                                const double* U, int ld, PcgWork w) {
+  if (op.kind == 0) return pcg_iteration_f64(st, m, n, op.A, op.lda, op.D, ell, U, ld, w, h->sd, h->si, h->red);
+  return pcg_iteration_lp(st, m, n, op.lp, ell, U, ld, w, h->sd, h->si, h->red);
+}
+
+// Build (or reuse) the graph "while (!done) { one PCG iteration }" for this
+// operator.  Returns false when graphs are unavailable (the caller then
+// issues iterations from the host).
+bool ensure_pcg_graph(nys_solver* h, int m, int n, const OpSpec& op, int ell, const double* U, int ld) {
+  if (!h->use_graphs) return false;
+  const double* D = op.kind == 0 ? op.D : reinterpret_cast<const double*>(op.lp.Df);
+  const long long lda = op.kind == 0 ? op.lda : op.lp.lda;
+  if (h->pcg_exec && h->gk_op == op.kind && h->gk_A == op.key() && h->gk_lda == lda && h->gk_m == m &&
+      h->gk_n == n && h->gk_ell == ell && h->gk_D == D && h->gk_U == U && h->gk_ld == ld)
+    return true;
+  drop_pcg_graph(h);
   PcgWork w = h->pw;
-  w.x = out;
+  w.x = h->pcg_x;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle cond{};
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node{};
+  ok = ok && cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const unsigned long long c0 = g_launches.load();
+      cudaError_t e1 = issue_pcg_iteration(h, h->cap_stream, m, n, op, ell, U, ld, w);
+      cudaError_t e2 = pcg_loop_condition(h->cap_stream, cond, h->si);
+      h->g_kernels_per_iter = (unsigned)(g_launches.load() - c0);
+      g_launches.fetch_sub(h->g_kernels_per_iter);   // counted when the graph runs
+      cudaGraph_t out = nullptr;
+      cudaError_t e3 = cudaStreamEndCapture(h->cap_stream, &out);
+      ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    h->use_graphs = false;
+    return false;
+  }
+  h->pcg_graph = g;
+  h->pcg_exec = exec;
+  h->gk_op = op.kind;
+  h->gk_A = op.key(); h->gk_lda = lda; h->gk_m = m; h->gk_n = n; h->gk_ell = ell;
+  h->gk_D = D; h->gk_U = U; h->gk_ld = ld;
+  return true;
+}
+
+// Run PCG on (A D A^T + delta I) dy = xi; dy is written into `out`.
+int run_pcg(nys_solver* h, int m, int n, const OpSpec& op, double delta, int ell, const double* U, int ld,
+            const double* lamh, const double* xi, double* out, double eta, int max_iter, int forced,
+            int* iters) {
+  PcgWork w = h->pw;
+  w.x = h->pcg_x;
   CK(pcg_setup_f64(h->st, m, ell, U, ld, lamh, delta, xi, eta, max_iter, forced, w, h->sd, h->si, h->red));
   const int limit = forced >= 0 ? forced : max_iter;
-  int issued = 0, chunk = 2;
-  while (true) {
+  if (ensure_pcg_graph(h, m, n, op, ell, U, ld)) {
+    CK(cudaGraphLaunch(h->pcg_exec, h->st));
+    CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
     int rc = sync_scalars(h, 0);
     if (rc != NYS_OK) return rc;
-    if (h->h_si[SI_DONE] || issued >= limit) break;
-    const int todo = std::min(chunk, limit - issued);
-    for (int k = 0; k < todo; ++k)
-      CK(pcg_iteration_f64(h->st, m, n, A, lda, D, delta, ell, U, ld, w, h->sd, h->si, h->red));
-    issued += todo;
-    chunk = std::min(chunk * 2, 16);
+    const int it = h->h_si[SI_ITERS];
+    count_launches(h->g_kernels_per_iter * (unsigned)std::max(it, 1));
+  } else {
+    int issued = 0, chunk = 2;
+    while (true) {
+      int rc = sync_scalars(h, 0);
+      if (rc != NYS_OK) return rc;
+      if (h->h_si[SI_DONE] || issued >= limit) break;
+      const int todo = std::min(chunk, limit - issued);
+      for (int k = 0; k < todo; ++k) CK(issue_pcg_iteration(h, h->st, m, n, op, ell, U, ld, w));
+      issued += todo;
+      chunk = std::min(chunk * 2, 16);
+    }
+    CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
   }
   *iters = h->h_si[SI_ITERS];
   if (forced < 0 && *iters >= max_iter) {
@@ -201,6 +356,17 @@ int run_pcg(nys_solver* h, int m, int n, const double* A, long long lda, const d
     if (!(h->h_red[SD_RR] <= h->h_red[SD_ETA2] * h->h_red[SD_BNORM2])) return NYS_WARN_PCG_MAXITER;
   }
   return NYS_OK;
+}
+
+int run_pcg(nys_solver* h, int m, int n, const double* A, long long lda, const double* D, double delta,
+            int ell, const double* U, int ld, const double* lamh, const double* xi, double* out, double eta,
+            int max_iter, int forced, int* iters) {
+  OpSpec op{};
+  op.kind = 0;
+  op.A = A;
+  op.lda = lda;
+  op.D = D;
+  return run_pcg(h, m, n, op, delta, ell, U, ld, lamh, xi, out, eta, max_iter, forced, iters);
 }
 
 // Algorithm 4: Newton direction through the normal equations.
@@ -215,6 +381,130 @@ int newton(nys_solver* h, int m, int n, const double* A, long long lda, const do
   CK(gemv_t_f64(h->st, m, n, A, lda, dy, nullptr, h->g_n, h->split_buf, h->split_cap));
   CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
   return rc;
+}
+
+// ---------------------------------------------------------------- precision form
+// Problem view shared by both forms.
+struct Prob {
+  int m, n;
+  int lp;                 // 0: FP64 A; 1: FP32 A with BF16 copies
+  const double* A64;
+  const float* Af;
+  long long lda;
+};
+
+// out = A x + beta v (accurate: FP64 A, or FP32 A with float-float sums)
+int op_Ax(nys_solver* h, const Prob& P, const double* x, double beta, const double* v, double* out) {
+  if (!P.lp) {
+    CK(gemv_n_f64(h->st, P.m, P.n, P.A64, P.lda, x, beta, v, out));
+  } else {
+    CK(split_ff(h->st, P.n, (int)align_up(P.n, 8), x, nullptr, h->fh, h->fl));
+    CK(gemv_rows_ff(h->st, P.m, P.n, P.Af, P.lda, h->fh, h->fl, nullptr, beta, v, out));
+  }
+  return NYS_OK;
+}
+
+// out = scale .* (A^T y)
+int op_Aty(nys_solver* h, const Prob& P, const double* y, const double* scale, double* out) {
+  if (!P.lp) {
+    CK(gemv_t_f64(h->st, P.m, P.n, P.A64, P.lda, y, scale, out, h->split_buf, h->split_cap));
+  } else {
+    CK(split_ff(h->st, P.m, (int)align_up(P.m, 8), y, nullptr, h->fh, h->fl));
+    CK(gemv_rows_ff(h->st, P.n, P.m, h->AfT, h->ld_ft, h->fh, h->fl, scale, 0.0, nullptr, out));
+  }
+  return NYS_OK;
+}
+
+// Y = A (D .* (A^T Omega_k)) into h->Y, Omega_k into h->Om (FP64 panels).
+int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D) {
+  const nys_options& o = h->opt;
+  CK(gaussian_omega(h->st, o.seed, k, P.m, ell, h->Om, h->ld));
+  if (!P.lp) {
+    CK(sketch_f64(h->st, P.m, P.n, P.A64, P.lda, D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf,
+                  h->split_cap));
+    return NYS_OK;
+  }
+  // Omega rounded to BF16 (both views then hold the same test matrix)
+  CK(round_panel_bf16(h->st, P.m, ell, h->Om, h->ld, h->Omb, (int)h->ld_om));
+  int S = 0;
+  int* err = h->si + SI_ERR;
+  // T (n x ell) = A^T Omega on the tensor cores; T' = BF16(D .* T)
+  CK(umma_gemm_bf16(h->st, P.n, ell, P.m, h->AbT, h->ld_bt, h->Omb, h->ld_om, h->upart, h->upart_cap,
+                    h->num_sms, &S, err));
+  CK(umma_reduce(h->st, P.n, ell, S, h->upart, 1, D, h->Tb, h->ld_tb));
+  // Y (m x ell) = A T'
+  CK(umma_gemm_bf16(h->st, P.m, ell, P.n, h->Ab, h->ld_b, h->Tb, h->ld_tb, h->upart, h->upart_cap,
+                    h->num_sms, &S, err));
+  CK(umma_reduce(h->st, P.m, ell, S, h->upart, 0, nullptr, h->Y32, h->ld));
+  CK(panel_f32_to_f64(h->st, P.m, ell, h->Y32, h->ld, h->Y, h->ld));
+  return NYS_OK;
+}
+
+// Precision-form Newton direction: Algorithm 4 with the normal equations
+// solved by iterative refinement.  xi, the refinement residual and the back
+// substitution use the FP32 problem matrix with float-float accumulation; the
+// corrections come from Nystrom PCG on the BF16 operator (FP32 once the
+// refinement stops contracting).
+int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, const double* D, double delta,
+              const double* r_d, const double* r_p, const double* r_xz, int ell, double eta, int max_iter,
+              double* dx, double* dy, double* dz, int* iters, int* refine) {
+  const int m = P.m, n = P.n;
+  CK(newton_rhs_f64(h->st, n, D, r_d, r_xz, x, h->t_n));
+  int rc = op_Ax(h, P, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi);
+  if (rc != NYS_OK) return rc;
+  CK(dot_f64(h->st, m, h->xi, h->xi, h->red_out + 12, h->red));
+  rc = sync_scalars_at(h, 12, 1);
+  if (rc != NYS_OK) return rc;
+  const double xin = std::sqrt(h->h_red[12]);
+  CK(cudaMemsetAsync(h->dyacc, 0, sizeof(double) * m, h->st));
+  CK(cudaMemcpyAsync(h->rr, h->xi, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  CK(to_f32(h->st, n, (int)align_up(n, 8), D, nullptr, h->Df));
+  double rn = xin, rn_prev = xin;
+  int total = 0, steps = 0, warn = NYS_OK;
+  bool fp32_inner = false;
+  const int max_steps = 12;
+  while (xin > 0.0 && rn > eta * xin && steps < max_steps) {
+    OpSpec op{};
+    op.kind = fp32_inner ? 2 : 1;
+    op.lp.bf16 = fp32_inner ? 0 : 1;
+    op.lp.A = fp32_inner ? (const void*)P.Af : (const void*)h->Ab;
+    op.lp.lda = fp32_inner ? P.lda : h->ld_b;
+    op.lp.AT = fp32_inner ? (const void*)h->AfT : (const void*)h->AbT;
+    op.lp.ldat = fp32_inner ? h->ld_ft : h->ld_bt;
+    op.lp.Df = h->Df;
+    op.lp.xf = h->xf;
+    op.lp.tf = h->tf;
+    op.lp.ld_mpad = (int)h->ld_bt;
+    const double eta_in = std::min(0.5, std::max(1e-4, 0.5 * eta * xin / rn));
+    int it = 0;
+    rc = run_pcg(h, m, n, op, delta, ell, h->U, h->ld, h->lamh, h->rr, h->ecorr, eta_in, max_iter, -1, &it);
+    if (rc < 0) return rc;
+    if (rc > 0) warn = rc;
+    total += it;
+    ++steps;
+    CK(axpby_f64(h->st, m, 1.0, h->ecorr, 1.0, h->dyacc, h->dyacc));
+    // r = xi - (A D A^T + delta I) dy  (FP32 A, float-float sums)
+    rc = op_Aty(h, P, h->dyacc, D, h->u_n);
+    if (rc != NYS_OK) return rc;
+    rc = op_Ax(h, P, h->u_n, delta, h->dyacc, h->nd_m);
+    if (rc != NYS_OK) return rc;
+    CK(axpby_f64(h->st, m, 1.0, h->xi, -1.0, h->nd_m, h->rr));
+    CK(dot_f64(h->st, m, h->rr, h->rr, h->red_out + 12, h->red));
+    rc = sync_scalars_at(h, 12, 1);
+    if (rc != NYS_OK) return rc;
+    rn_prev = rn;
+    rn = std::sqrt(h->h_red[12]);
+    if (!std::isfinite(rn)) return fail(h, NYS_ERR_NUMERIC, "non-finite refinement residual");
+    if (rn > 0.5 * rn_prev) fp32_inner = true;   // BF16 corrections no longer contract
+  }
+  if (xin > 0.0 && rn > eta * xin && warn == NYS_OK) warn = NYS_WARN_PCG_MAXITER;
+  CK(cudaMemcpyAsync(dy, h->dyacc, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  rc = op_Aty(h, P, dy, nullptr, h->g_n);
+  if (rc != NYS_OK) return rc;
+  CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
+  *iters = total;
+  *refine = steps;
+  return warn;
 }
 
 }  // namespace
@@ -247,7 +537,8 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   if (!out) return NYS_ERR_ARG;
   *out = nullptr;
   if (!opt || max_m <= 0 || max_n <= 0 || max_batch < 0 || opt->ell <= 0 || opt->tol <= 0.0 ||
-      opt->max_ipm_iter < 0 || opt->max_pcg_iter < 0 || opt->precision_mode != 0)
+      opt->max_ipm_iter < 0 || opt->max_pcg_iter < 0 || opt->precision_mode < 0 ||
+      opt->precision_mode > 1 || (opt->precision_mode == 1 && opt->ell > 512))
     return NYS_ERR_ARG;
   nys_solver* h = new nys_solver();
   h->opt = *opt;
@@ -275,6 +566,23 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
     delete h;
     return NYS_ERR_NOMEM;
   }
+  if (opt->precision_mode == 1) {
+    h->lp_bytes = carve_lp(h, nullptr);
+    if (cudaMalloc(&h->lp_arena, h->lp_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(h->arena);
+      delete h;
+      return NYS_ERR_NOMEM;
+    }
+    carve_lp(h, static_cast<char*>(h->lp_arena));
+    cudaMemsetAsync(h->lp_arena, 0, h->lp_bytes, h->st);
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(h->arena);
+    delete h;
+    return NYS_ERR_CUDA;
+  }
+  if (const char* env = std::getenv("NYS_NO_GRAPHS")) h->use_graphs = (env[0] == '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess) {
     cudaFree(h->arena);
@@ -289,7 +597,10 @@ int nys_destroy(nys_handle h) {
   if (!h) return NYS_ERR_ARG;
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  drop_pcg_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   cudaFree(h->arena);
+  if (h->lp_arena) cudaFree(h->lp_arena);
   if (h->stage) cudaFree(h->stage);
   cudaFreeHost(h->h_red);
   cudaFreeHost(h->h_si);
@@ -395,6 +706,23 @@ int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long
                 ld, lam, eta, max_iter, forced_iters, dx, dy, dz, iters);
 }
 
+int nys_gemm_bf16(nys_handle h, int M, int N, int K, const void* A, long long lda, const void* B,
+                  long long ldb, float* C, long long ldc) {
+  if (!h) return NYS_ERR_ARG;
+  if (M <= 0 || N <= 0 || N > 512 || K <= 0 || !A || !B || !C || lda < K || ldb < K || ldc < M ||
+      lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(B) & 15u))
+    return fail(h, NYS_ERR_ARG, "nys_gemm_bf16: bad argument");
+  float* part = h->upart ? h->upart : reinterpret_cast<float*>(h->split_buf);
+  const size_t cap = h->upart ? h->upart_cap : 2 * h->split_cap;
+  const size_t npad = (size_t)(N + 15) / 16 * 16;
+  if (npad * (size_t)M > cap) return fail(h, NYS_ERR_ARG, "nys_gemm_bf16: M x N exceeds the workspace");
+  CK(cudaMemsetAsync(h->si + SI_ERR, 0, sizeof(int), h->st));
+  int S = 0;
+  CK(umma_gemm_bf16(h->st, M, N, K, A, lda, B, ldb, part, cap, h->num_sms, &S, h->si + SI_ERR));
+  CK(umma_reduce(h->st, M, N, S, part, 0, nullptr, C, ldc));
+  return sync_scalars(h, 0);
+}
+
 int nys_step_length(nys_handle h, int n, const double* v, const double* dv, double* alpha) {
   if (!h) return NYS_ERR_ARG;
   if (n <= 0 || !v || !dv || !alpha) return fail(h, NYS_ERR_ARG, "nys_step_length: bad argument");
@@ -411,11 +739,12 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!p || !r) return fail(h, NYS_ERR_ARG, "nys_solve: null problem or result");
   const int m = p->m, n = p->n;
-  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n || p->a_dtype != NYS_F64 ||
-      !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 || !p->z0 || !r->x || !r->y || !r->z ||
-      p->k0 < 0)
-    return fail(h, NYS_ERR_ARG, "nys_solve: bad problem (sizes, dtype or null pointers)");
   const nys_options& o = h->opt;
+  const int lp = o.precision_mode == 1;
+  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n ||
+      p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 ||
+      !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0)
+    return fail(h, NYS_ERR_ARG, "nys_solve: bad problem (sizes, dtype for the precision mode, or null pointers)");
   const int ell = std::min(h->ell_cap, m);
   const long long lda = p->lda;
   r->status = NYS_OK;
@@ -425,9 +754,11 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   r->pcg_log_len = 0;
 
   // Problem data on the device (staged when the caller passes host memory).
-  const double *A = static_cast<const double*>(p->A), *b = p->b, *c = p->c, *q = p->q;
+  const size_t esz = lp ? sizeof(float) : sizeof(double);
+  const void* Av = p->A;
+  const double *b = p->b, *c = p->c, *q = p->q;
   if (p->host) {
-    const size_t a_bytes = align_up((size_t)m * lda * sizeof(double), 256);
+    const size_t a_bytes = align_up((size_t)m * lda * esz, 256);
     const size_t need = a_bytes + 3 * align_up(sizeof(double) * (size_t)n, 256) +
                         align_up(sizeof(double) * (size_t)m, 256);
     if (need > h->stage_bytes) {
@@ -441,16 +772,20 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
       h->stage_bytes = need;
     }
     char* s = static_cast<char*>(h->stage);
-    double* dA = reinterpret_cast<double*>(s);
+    void* dA = s;
     double* db = reinterpret_cast<double*>(s + a_bytes);
     double* dc = reinterpret_cast<double*>(s + a_bytes + align_up(sizeof(double) * m, 256));
     double* dq = reinterpret_cast<double*>(reinterpret_cast<char*>(dc) + align_up(sizeof(double) * n, 256));
-    CK(cudaMemcpyAsync(dA, p->A, (size_t)m * lda * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(dA, p->A, (size_t)m * lda * esz, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(db, p->b, sizeof(double) * m, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(dc, p->c, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(dq, p->q, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
-    A = dA; b = db; c = dc; q = dq;
+    Av = dA; b = db; c = dc; q = dq;
   }
+  Prob P{m, n, lp, lp ? nullptr : static_cast<const double*>(Av), lp ? static_cast<const float*>(Av) : nullptr, lda};
+  const double* A = P.A64;
+  if (lp)   // BF16 A and A^T for the inner solves and the sketch, FP32 A^T for residuals
+    CK(convert_transpose(h->st, m, n, 0, Av, lda, h->Ab, h->ld_b, h->AbT, h->ld_bt, h->AfT, h->ld_ft));
   const cudaMemcpyKind kin = p->host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(h->x, p->x0, sizeof(double) * n, kin, h->st));
   CK(cudaMemcpyAsync(h->y, p->y0, sizeof(double) * m, kin, h->st));
@@ -484,8 +819,9 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
 
   while (true) {
     // Residuals and duality measure at the current iterate.
-    CK(gemv_n_f64(h->st, m, n, A, lda, h->x, 0.0, nullptr, h->Ax));
-    CK(gemv_t_f64(h->st, m, n, A, lda, h->y, nullptr, h->Aty, h->split_buf, h->split_cap));
+    rc = op_Ax(h, P, h->x, 0.0, nullptr, h->Ax);
+    if (rc == NYS_OK) rc = op_Aty(h, P, h->y, nullptr, h->Aty);
+    if (rc != NYS_OK) { status = rc; break; }
     CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
                          rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
     rc = sync_scalars(h, 3);
@@ -532,17 +868,21 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
 
     // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).
     CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
-    CK(gaussian_omega(h->st, o.seed, p->k0 + k, m, ell, h->Om, h->ld));
-    CK(sketch_f64(h->st, m, n, A, lda, h->D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf,
-                  h->split_cap));
+    rc = op_sketch(h, P, p->k0 + k, ell, h->D);
+    if (rc != NYS_OK) { status = rc; break; }
     CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
                         h->cw, h->num_sms));
     const double eta = std::max(1e-10, std::min(1e-2, 0.1 * mu));
 
     // Predictor (Algorithm 5, first step).
-    int it = 0;
-    rc = newton(h, m, n, A, lda, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, h->U, h->ld,
-                h->lamh, eta, o.max_pcg_iter, next_forced(), h->dxp, h->dyp, h->dzp, &it);
+    int it = 0, ref = 0;
+    if (lp)
+      rc = newton_lp(h, P, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, eta, o.max_pcg_iter,
+                     h->dxp, h->dyp, h->dzp, &it, &ref);
+    else
+      rc = newton(h, m, n, A, lda, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, h->U, h->ld,
+                  h->lamh, eta, o.max_pcg_iter, next_forced(), h->dxp, h->dyp, h->dzp, &it);
+    r->refine_steps += ref;
     if (rc < 0) { status = rc; break; }
     if (rc > 0) warn = rc;
     log_pcg(it);
@@ -559,8 +899,13 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
 
     // Corrector (Eq. corrector-RHS): r_d = r_p = 0, r_xz = mu_t - dxp dzp.
     CK(corrector_rhs_f64(h->st, n, mu_t, h->dxp, h->dzp, h->r_xz));
-    rc = newton(h, m, n, A, lda, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, h->U, h->ld,
-                h->lamh, eta, o.max_pcg_iter, next_forced(), h->dxc, h->dyc, h->dzc, &it);
+    if (lp)
+      rc = newton_lp(h, P, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, eta, o.max_pcg_iter,
+                     h->dxc, h->dyc, h->dzc, &it, &ref);
+    else
+      rc = newton(h, m, n, A, lda, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, h->U, h->ld,
+                  h->lamh, eta, o.max_pcg_iter, next_forced(), h->dxc, h->dyc, h->dzc, &it);
+    r->refine_steps += ref;
     if (rc < 0) { status = rc; break; }
     if (rc > 0) warn = rc;
     log_pcg(it);

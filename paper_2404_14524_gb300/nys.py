@@ -94,6 +94,7 @@ _SIGS = {
     "nys_newton": (_I, [_P, _I, _I, _I, _P, _LL, _P, _P, _P, _D, _P, _P, _P, _I, _P, _I, _P, _D,
                         _I, _I, _P, _P, _P, ctypes.POINTER(_I)]),
     "nys_step_length": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
+    "nys_gemm_bf16": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL]),
 }
 
 
@@ -283,6 +284,19 @@ def nys_newton(h: Handle, A, x, z, D, delta, r_d, r_p, r_xz, U, lam, eta, max_it
     return dx, dy, dz, it.value
 
 
+def nys_gemm_bf16(h: Handle, A, B, out=None):
+    """C = A B^T (A: M x K, B: N x K, torch.bfloat16 row-major) on the tensor
+    cores; returns C as an (N, M) float32 tensor (column-major M x N)."""
+    M, K = A.shape
+    N = B.shape[0]
+    for t, nm in ((A, "A"), (B, "B")):
+        if t.dtype != torch.bfloat16 or t.stride(1) != 1:
+            raise TypeError(f"{nm} must be a row-major bfloat16 tensor")
+    out = torch.empty((N, M), dtype=torch.float32, device=A.device) if out is None else out
+    h.check(lib().nys_gemm_bf16(h.h, M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(out), M))
+    return out
+
+
 def nys_step_length(h: Handle, v, dv) -> float:
     a = ctypes.c_double()
     h.check(lib().nys_step_length(h.h, v.numel(), _ptr(_f64(v, "v")), _ptr(_f64(dv, "dv")),
@@ -300,7 +314,14 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     m, n = A.shape
     host = not A.is_cuda
     dev = None if host else A.device
-    for t, nm in ((A, "A"), (b, "b"), (c, "c"), (q, "q"), (x0, "x0"), (y0, "y0"), (z0, "z0")):
+    if A.dtype == torch.float32:          # precision form: FP32 A defines the problem
+        a_dtype = NYS_F32
+        if A.stride(1) != 1:
+            raise ValueError("A must be row-major")
+    else:
+        a_dtype = NYS_F64
+        _f64(A, "A", dev if not host else torch.device("cpu"))
+    for t, nm in ((b, "b"), (c, "c"), (q, "q"), (x0, "x0"), (y0, "y0"), (z0, "z0")):
         _f64(t, nm, dev if not host else torch.device("cpu"))
     mk = (lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True)) if host else \
         (lambda k: torch.empty(k, dtype=torch.float64, device=dev))
@@ -309,7 +330,7 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     for t, nm in ((lam0, "lam0"), (zeta0, "zeta0")):
         if t is not None:
             _f64(t, nm, dev if not host else torch.device("cpu"))
-    p = Problem(m=m, n=n, a_dtype=NYS_F64, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(),
+    p = Problem(m=m, n=n, a_dtype=a_dtype, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(),
                 c=c.data_ptr(), q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(),
                 z0=z0.data_ptr(), host=1 if host else 0,
                 lam0=lam0.data_ptr() if lam0 is not None else None,

@@ -1,0 +1,73 @@
+"""The precision form: tcgen05 BF16 sketch products and the BF16 + refinement
+Newton solve, against the FP64 CPU oracle on the FP32 problem matrix."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import nys_oracle as O
+from paper_2404_14524_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def nys():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_14524_gb300 import build
+    build.build()
+    from paper_2404_14524_gb300 import nys as N
+    N.lib()
+    return N
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (300, 40, 1000), (777, 256, 2048), (1000, 416, 5000),
+                                   (129, 400, 4100), (2000, 100, 20001)])
+def test_tensor_core_gemm_matches_fp64(nys, M, N, K):
+    """tcgen05 kind::f16 BF16 products (FP32 accumulation) against an FP64
+    product of the same BF16 values; bound: K * 2^-24 growth on sum |a b|."""
+    g = torch.Generator().manual_seed(M + N + K)
+    ldk = (K + 7) // 8 * 8
+    A = torch.zeros(M, ldk, dtype=torch.bfloat16)
+    B = torch.zeros(N, ldk, dtype=torch.bfloat16)
+    A[:, :K] = (torch.rand(M, K, generator=g) - 0.5).to(torch.bfloat16)
+    B[:, :K] = (torch.rand(N, K, generator=g) - 0.5).to(torch.bfloat16)
+    h = nys.Handle(16384, 4096, ell=8)
+    Ad, Bd = A.to(DEV), B.to(DEV)
+    C = nys.nys_gemm_bf16(h, Ad[:, :K] if ldk == K else Ad.narrow(1, 0, K), Bd.narrow(1, 0, K)).cpu().double()
+    ref = (A[:, :K].double() @ B[:, :K].double().T).T
+    bound = (A[:, :K].double().abs() @ B[:, :K].double().abs().T).T
+    err = (C - ref).abs()
+    assert float((err - 4 * K * 2.0 ** -24 * bound).max()) <= 1e-6
+
+
+def _qp32(seed, m, n):
+    qp = synth.workload_precision_scaled(seed=seed, m=m, n=n)
+    A32 = qp.A.astype(np.float32)                 # the FP32 matrix defines the problem
+    A64 = A32.astype(np.float64)
+    b = A64 @ qp.x0                               # keep the start feasible for the FP32 matrix
+    c = A64.T @ qp.y0 + qp.z0 - qp.q * qp.x0
+    return A32, A64, b, c, qp
+
+
+def test_precision_form_meets_kkt_and_tracks_the_fp64_oracle(nys):
+    """BF16 inner PCG + FP32/float-float refinement: KKT <= 1e-6 on the FP32
+    problem, and the solution agrees with the FP64 oracle's to the tolerance
+    level (both stop at tol 1e-6 on different iterates)."""
+    m, n, ell, tol = 600, 3000, 30, 1e-6
+    A32, A64, b, c, qp = _qp32(31, m, n)
+    ref = O.solve(A64, b, c, qp.q, qp.x0, qp.y0, qp.z0, O.Options(tol=tol, ell=ell, seed=5))
+    assert ref.status == "converged"
+    h = nys.Handle(m, n, ell=ell, tol=tol, seed=5, precision_mode=1)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    x, y, z, info = nys.nys_solve(h, T(A32), T(b), T(c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    assert info["status"] == 0, info
+    xs, ys, zs = (t.cpu().numpy() for t in (x, y, z))
+    rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, xs, ys, zs)
+    assert rp <= tol and rd <= tol and mu <= tol
+    err = np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)
+    print(f"precision form: {info['ipm_iters']} IPM, {info['pcg_iters_total']} PCG, "
+          f"{info['refine_steps']} refinement steps; |x - x_oracle| / |x| = {err:.2e}")
+    assert err <= 1e-3
+    assert info["refine_steps"] >= 2 * info["ipm_iters"]
