@@ -416,3 +416,37 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
 def solve_qp(qp, opt: Options, **kw) -> Result:
     """Convenience wrapper over a workload record with fields A, b, c, q, x0, y0, z0."""
     return solve(qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0, opt, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Differentiation through the solution (transposed KKT system).
+#
+# At the final iterate the regularised Newton matrix of Eq. Newton,
+#   J = [[Q + rho I, -A^T, -I], [A, delta I, 0], [Z, 0, X]],
+# is the Jacobian of the (perturbed) optimality conditions of (P)/(D) with
+# respect to (x, y, z).  For a loss L(x*) with g = dL/dx*, the implicit
+# function theorem gives dL/dtheta = -lam^T dF/dtheta with J^T lam = (g, 0, 0).
+# READING: the adjoint uses the final rho, delta and (x, z) of the solve.
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Gradients:
+    c: np.ndarray
+    b: np.ndarray
+    q: np.ndarray
+    A: np.ndarray
+
+
+def kkt_adjoint(A, x, y, z, q, rho, delta, g) -> Gradients:
+    """Dense transposed-KKT solve (LU) for the gradients of L(x*):
+    dL/dc = -lam1, dL/db = lam2, dL/dq = -lam1 .* x, dL/dA = y lam1^T - lam2 x^T."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    J = np.block([
+        [np.diag(q + rho), -A.T, -np.eye(n)],
+        [A, delta * np.eye(m), np.zeros((m, n))],
+        [np.diag(z), np.zeros((n, m)), np.diag(x)],
+    ])
+    lam = np.linalg.solve(J.T, np.concatenate([g, np.zeros(m), np.zeros(n)]))
+    l1, l2 = lam[:n], lam[n:n + m]
+    return Gradients(c=-l1, b=l2, q=-l1 * x, A=np.outer(y, l1) - np.outer(l2, x))
