@@ -4,19 +4,20 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload NAME]
 
-A step is one whole Nys-IP-PMM solve of a synthetic separable QP (every
-Newton system through the Nystrom sketch, core factorisation, PCG, back
-substitution and step lengths), inputs resident in HBM.  Multi-GPU runs are
-independent replicas (one QP per rank, no collective on the data path):
-`value` = solves of all ranks / max-over-ranks time.
+A step is one whole Nys-IP-PMM solve of the workload (every Newton system
+through the Nystrom sketch, the core factorisation, PCG, back substitution
+and the step lengths; for the batch workload all of its QPs; for the
+differentiation workload the forward solves plus the adjoint solves), with
+the inputs resident in HBM.  Multi-GPU runs are independent replicas (one
+workload per rank, no collective on the data path): `value` = solves of all
+ranks / max-over-ranks time.
 
-Extra keys: `roofline` (normal-equations operator, the dominant kernel pair,
-timed with CUDA events on the solver's stream), `cpu_baseline` (the CPU
-oracle on a bounded sample, rank 0), `e2e` (the same solves through the C ABI
-with pinned host buffers, copies inside the timed region), `clocks`
-(nvidia-smi samples taken during the timed region) and `gpu_launches`
-(kernels of libnys.so launched inside the timed region).
-`--impl reference` times the CPU oracle instead (the reference arm).
+Extra keys: `roofline` (the dominant kernel, timed with CUDA events on the
+solver's stream), `cpu_baseline` (the CPU oracle on a bounded sample, rank 0,
+N=1), `e2e` (the same solves through the C ABI with pinned host buffers,
+copies inside the timed region), `clocks` (nvidia-smi samples taken during the
+timed region) and `gpu_launches` (kernels of libnys.so launched inside the
+timed region).  `--impl reference` times the CPU oracle instead.
 """
 from __future__ import annotations
 
@@ -35,36 +36,41 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-# name -> (generator kwargs, ell, tol, description)
+# name -> workload description
 WORKLOADS = {
-    "small-fp64": dict(gen=("workload_small", {}), ell=20, tol=1e-6,
-                       desc="m=200, n=500, sigma_i=1/i, q~U[0,1], ell=20, tol 1e-6, FP64"),
-    "fp64-5000x20000": dict(gen=("workload_fp64", {}), ell=100, tol=1e-8,
-                            desc="m=5000, n=20000, sigma_i=i^-0.8, q 50% zero, ell=100, tol 1e-8, FP64"),
-    "fp64-2000x10000-exp": dict(gen=("workload_precision_scaled", {}), ell=40, tol=1e-6,
-                                desc="m=2000, n=10000, sigma_i=exp(-i/200)+1e-3, q~U[0,1], ell=40, tol 1e-6, FP64"),
+    "small-fp64": dict(form="fp64", m=200, n=500, ell=20, tol=1e-6, gen="small",
+                       desc="m=200, n=500, sigma_i=1/i, q~U[0,1], ell=20, tol 1e-6, FP64 form"),
+    "fp64-5000x20000": dict(form="fp64", m=5000, n=20000, ell=100, tol=1e-8, gen="fp64",
+                            desc="m=5000, n=20000, sigma_i=i^-0.8, q 50% zero, ell=100, tol 1e-8, FP64 form"),
+    "precision-20000x100000": dict(form="bf16", m=20000, n=100000, ell=400, tol=1e-6, gen="device-exp200",
+                                   desc="m=20000, n=100000, sigma_i=exp(-i/200)+1e-3, q~U[0,1], FP32 A stored "
+                                        "BF16, FP32/float-float refinement, ell=400, tol 1e-6"),
+    "precision-4000x20000": dict(form="bf16", m=4000, n=20000, ell=80, tol=1e-6, gen="device-exp200",
+                                 desc="m=4000, n=20000 (scaled precision workload), ell=80, tol 1e-6"),
+    "batch-256": dict(form="batch", count=256, ell=32, tol=1e-6, gen="batch",
+                      desc="256 QPs, m~U{64..1024}, n~U{4m..8m}, sigma_i=1/i, q~U[0,1], "
+                           "ell=min(32, m/4), tol 1e-6, FP64 form, nys_solve_batched"),
+    "diff-64x512x2048": dict(form="diff", count=64, m=512, n=2048, ell=32, tol=1e-8, gen="diff",
+                             desc="64 Gaussian QPs 512x2048, q~U[0.1,1], forward tol 1e-8 + adjoint "
+                                  "(dL/d(c,b,q,A), L=||x*-x_t||^2)"),
 }
-DEFAULT_WORKLOAD = "fp64-2000x10000-exp"
+DEFAULT_WORKLOAD = "small-fp64"
 
-# FP64 ALU peak: 152 SMs x 2 DFMA/clk/SM x 2 flop at the 2070 MHz maximum SM
-# clock (the nominal 1.25 TFLOP/s FP64 of GB300 expressed in unit counts).
-DFMA_PER_CLK_PER_SM = 2
 SMS = 152
 SM_MAX_MHZ = 2070.0
+DFMA_PER_CLK_PER_SM = 2        # GB300: 1.25 TFLOP/s FP64 nominal = 152 x 2 x 2 x 2.07 GHz
 
 
 def fp64_alu_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
     return SMS * DFMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
-def make_qp(name: str, rank: int):
-    from paper_2404_14524_gb300 import synth
-    w = WORKLOADS[name]
-    fn, kw = w["gen"]
-    kw = dict(kw)
-    base = {"workload_small": 1235, "workload_fp64": 1236, "workload_precision_scaled": 1237}[fn]
-    kw["seed"] = base + 1000 * rank          # replicas solve different QPs
-    return getattr(synth, fn)(**kw)
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6681.5), d.get("bf16_tflops", 1873.8), "measured"
+    return 6800.0, 1900.0, "fallback"
 
 
 class ClockSampler:
@@ -74,9 +80,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.path = None
+        self.index, self.proc, self.path = index, None, None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -108,99 +112,146 @@ class ClockSampler:
             os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        num = lambda v: v.replace(".", "", 1).isdigit()
+        sm = [float(r[0]) for r in rows if num(r[0])]
+        smax = [float(r[1]) for r in rows if num(r[1])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_record(kernel_file: str):
-    """dram bytes per launch of the operator from the committed ncu summary,
+def traffic_record(kernel_file: str, key: str):
+    """dram bytes per unit of work of a kernel from the committed ncu summary,
     or None when the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
+    rec = json.load(open(path)).get(key)
+    if not rec:
+        return None
     src = open(os.path.join(ROOT, "paper_2404_14524_gb300", "csrc", kernel_file), "rb").read()
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return rec
 
 
-def cpu_baseline(qp, w, gpu_ipm: int, gpu_pcg: int, seed: int):
-    """The oracle as it stands on this host.  Whole solve when that is short;
-    otherwise timed components extrapolated with the GPU run's counts."""
+# ------------------------------------------------------------------ workloads
+
+def host_workload(w, rank):
+    """numpy problems (list) for the host-generated workloads."""
+    from paper_2404_14524_gb300 import synth
+    g = w["gen"]
+    off = 1000 * rank
+    if g == "small":
+        return [synth.workload_small(1235 + off)]
+    if g == "fp64":
+        return [synth.workload_fp64(1236 + off)]
+    if g == "batch":
+        return synth.workload_batch(1238 + off, count=w["count"])
+    if g == "diff":
+        qps, targets = synth.workload_diff(1239 + off, count=w["count"], m=w["m"], n=w["n"])
+        for qp, t in zip(qps, targets):
+            qp.target = t
+        return qps
+    return None
+
+
+def device_workload(w, rank, dev):
+    from paper_2404_14524_gb300 import synth
+    import torch
+    A, b, c, q, x0, y0, z0 = synth.spectral_qp_device(1237 + 1000 * rank, w["m"], w["n"], "exp200", "uniform",
+                                                      device=dev, dtype=torch.float32)
+    torch.cuda.synchronize(dev)
+    return A, b, c, q, x0, y0, z0
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+
+def oracle_component_times(A64, b, c, q, x0, y0, z0, ell, tol, seed):
     from oracle import nys_oracle as O
-    threads = os.cpu_count()
-    m, n = qp.A.shape
-    # components: one IPM iteration with PCG forced to zero, and PCG iterations
+    m, n = A64.shape
     t0 = time.perf_counter()
-    O.solve_qp(qp, O.Options(tol=w["tol"], ell=w["ell"], seed=seed, forced_ipm=1, forced_pcg=[0, 0]))
+    O.solve(A64, b, c, q, x0, y0, z0, O.Options(tol=tol, ell=ell, seed=seed, forced_ipm=1, forced_pcg=[0, 0]))
     t_ipm = time.perf_counter() - t0
-    D = O.scaling_D(qp.x0, qp.z0, qp.q, 1.0)
-    F = O.nystrom(qp.A, D, O.gaussian_omega(seed, 0, m, min(w["ell"], m)))
+    D = O.scaling_D(x0, z0, q, 1.0)
+    F = O.nystrom(A64, D, O.gaussian_omega(seed, 0, m, min(ell, m)))
     xi = np.random.default_rng(0).standard_normal(m)
-    k_pcg = 20
+    k = 10
     t0 = time.perf_counter()
-    O.pcg(lambda v: O.normal_matvec(qp.A, D, 1e-3, v), lambda v: O.precond_inv_apply(F, 1e-3, v),
-          xi, 0.0, k_pcg, forced_iters=k_pcg)
-    t_pcg = (time.perf_counter() - t0) / k_pcg
-    est = gpu_ipm * t_ipm + gpu_pcg * t_pcg
-    sample = (f"1 oracle IPM iteration with PCG forced to 0 ({t_ipm:.3f} s) + {k_pcg} oracle PCG "
-              f"iterations ({t_pcg * 1e3:.2f} ms each) on the same {m}x{n} workload, extrapolated with "
-              f"the GPU run's counts ({gpu_ipm} IPM, {gpu_pcg} PCG iterations per solve)")
-    if est <= 30.0:
+    O.pcg(lambda v: O.normal_matvec(A64, D, 1e-3, v), lambda v: O.precond_inv_apply(F, 1e-3, v), xi, 0.0, k,
+          forced_iters=k)
+    return t_ipm, (time.perf_counter() - t0) / k
+
+
+def cpu_baseline(problems, w, runs, seed):
+    """The oracle as it stands on this host's cores: a whole solve when one
+    takes at most ~30 s (else timed components extrapolated with the GPU
+    run's iteration counts)."""
+    from oracle import nys_oracle as O
+    cores = os.cpu_count()
+    qp = problems[0]
+    A64 = qp["A64"]
+    t_ipm, t_pcg = oracle_component_times(A64, qp["b"], qp["c"], qp["q"], qp["x0"], qp["y0"], qp["z0"],
+                                          qp["ell"], w["tol"], seed)
+    ipm, pcg = runs[0]["ipm_iters"], runs[0]["pcg_iters_total"]
+    est = ipm * t_ipm + pcg * t_pcg
+    per_step = len(problems)
+    if est * per_step <= 30.0:
         t0 = time.perf_counter()
-        r = O.solve_qp(qp, O.Options(tol=w["tol"], ell=w["ell"], seed=seed))
+        for p in problems:
+            O.solve(p["A64"], p["b"], p["c"], p["q"], p["x0"], p["y0"], p["z0"],
+                    O.Options(tol=w["tol"], ell=p["ell"], seed=seed))
         full = time.perf_counter() - t0
-        return {"value": 1.0 / full, "unit": "QP solves/s", "cores": threads, "kind": "oracle",
-                "sample": f"one whole oracle solve of the same workload ({r.ipm_iters} IPM, "
-                          f"{sum(r.pcg_iters)} PCG iterations, {full:.2f} s)"}
-    return {"value": 1.0 / est, "unit": "QP solves/s", "cores": threads, "kind": "oracle",
-            "sample": sample}
+        return {"value": per_step / full / per_step, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
+                "sample": f"whole oracle solve(s) of the same workload ({per_step} QP, {full:.2f} s)"}
+    m, n = A64.shape
+    return {"value": 1.0 / est, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 oracle IPM iteration with PCG forced to 0 ({t_ipm:.3f} s) + 10 oracle PCG iterations "
+                      f"({t_pcg * 1e3:.2f} ms each) on the first {m}x{n} QP, extrapolated with the GPU run's "
+                      f"counts ({ipm} IPM, {pcg} PCG iterations per solve)"}
 
 
 def run_reference(args, w, rank, world):
-    """Reference arm: the CPU oracle, timed on the host cores (rank 0 only)."""
+    """Reference arm: the CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return
     from oracle import nys_oracle as O
-    qp = make_qp(args.workload, 0)
+    probs = host_workload(w, 0)
+    if probs is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm runs the host-generated "
+                          "workloads; this workload is generated on the GPU"}), flush=True)
+        return
     seed = 7
-    m, n = qp.A.shape
-    # bounded sample per step: at most `budget` seconds of oracle work
-    t0 = time.perf_counter()
-    r = O.solve_qp(qp, O.Options(tol=w["tol"], ell=w["ell"], seed=seed, max_ipm_iter=3))
-    probe = time.perf_counter() - t0
-    whole = probe < 20.0 / max(1, args.steps + args.warmup)
-    times = []
+    times, sample = [], ""
+    budget = 150.0 / max(1, args.steps + args.warmup)
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        if whole:
-            r = O.solve_qp(qp, O.Options(tol=w["tol"], ell=w["ell"], seed=seed))
-        else:
-            r = O.solve_qp(qp, O.Options(tol=w["tol"], ell=w["ell"], seed=seed, max_ipm_iter=3))
+        done = 0
+        for qp in probs:
+            ell = min(w["ell"], max(1, qp.m // 4)) if w["form"] == "batch" else w["ell"]
+            O.solve_qp(qp, O.Options(tol=w["tol"], ell=ell, seed=seed))
+            done += 1
+            if time.perf_counter() - t0 > budget:
+                break
         dt = time.perf_counter() - t0
         if s >= args.warmup:
-            times.append(dt)
+            times.append(dt / done)
+        sample = f"{done} of {len(probs)} QP(s) solved whole per step"
     per = statistics.mean(times)
-    if whole:
-        value, sample = 1.0 / per, f"whole oracle solve ({r.ipm_iters} IPM iterations) per step"
-    else:
-        value, sample = None, "first 3 oracle IPM iterations per step (whole solve exceeds the step budget)"
+    value = 1.0 / per
     line = {"metric": "QP solves/s to KKT tol", "value": value, "unit": "QP solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3 * len(probs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n},
-            "cpu_baseline": {"value": value, "unit": "QP solves/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "QP solves/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": args.workload, "desc": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "QP solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "QP solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------ GPU arm
 
 def main():
     ap = argparse.ArgumentParser()
@@ -210,13 +261,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="precision workloads: also time one FP64-form solve of the same QP")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
@@ -231,117 +282,211 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    qp = make_qp(args.workload, rank)
-    m, n = qp.A.shape
+    barrier = (lambda: dist.barrier()) if world > 1 else (lambda: None)
     seed = 7
-    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    A, b, c, q, x0, y0, z0 = (T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0))
+    form = w["form"]
     stream = torch.cuda.Stream(device=dev)
+
+    # ---- problems resident in HBM
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    host_probs = host_workload(w, rank)
+    if host_probs is not None:
+        dev_probs = []
+        for qp in host_probs:
+            ell = min(w["ell"], max(1, qp.m // 4)) if form == "batch" else w["ell"]
+            dev_probs.append(tuple(T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0)) + (ell,))
+    else:
+        dev_probs = [device_workload(w, rank, dev) + (w["ell"],)]
+    mmax = max(p[0].shape[0] for p in dev_probs)
+    nmax = max(p[0].shape[1] for p in dev_probs)
+    a_bytes = sum(p[0].numel() * p[0].element_size() for p in dev_probs)
+
     with torch.cuda.stream(stream):
-        h = nys.Handle(m, n, ell=w["ell"], tol=w["tol"], seed=seed, max_pcg_iter=1000, stream=stream)
+        if form == "batch":
+            h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=32, stream=stream)
+        else:
+            h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream,
+                           precision_mode=1 if form == "bf16" else 0)
+
+        def step():
+            if form == "batch":
+                return [r[3] for r in nys.nys_solve_batched(h, dev_probs)]
+            out = []
+            for pr in dev_probs:
+                x, y, z, info = nys.nys_solve(h, *pr[:7])
+                if form == "diff":
+                    g = 2.0 * (x - T(host_probs[len(out)].target))
+                    nys.nys_adjoint(h, pr[0], pr[3], x, y, z, info, g, eta=1e-10)
+                out.append(info)
+            return out
+
         for _ in range(args.warmup):
-            x, y, z, info = nys.nys_solve(h, A, b, c, q, x0, y0, z0)
+            step()
         torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
         l0 = nys.nys_kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        infos = []
+        runs = []
+        t_wall = time.perf_counter()
         with ClockSampler(local) as clk:
             e0.record(stream)
             for _ in range(args.steps):
-                x, y, z, info = nys.nys_solve(h, A, b, c, q, x0, y0, z0)
-                infos.append(info)
+                runs = step()
             e1.record(stream)
             torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
         barrier()
         torch.cuda.synchronize(dev)
         launches = nys.nys_kernel_launches() - l0
-        ms = e0.elapsed_time(e1)
+        # worker streams of the batch form are not ordered with `stream`: use the wall clock there
+        ms = t_wall * 1e3 if form == "batch" else e0.elapsed_time(e1)
         clocks = clk.summary()
-        t = torch.tensor([ms, float(launches)], dtype=torch.float64, device=dev)
         if world > 1:
-            tmax = t.clone()
+            t = torch.tensor([ms, float(launches)], dtype=torch.float64, device=dev)
+            tmax, tsum = t.clone(), t.clone()
             dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-            tsum = t.clone()
             dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
             ms, launches = float(tmax[0]), int(tsum[1])
-        value = args.steps * world / (ms / 1e3)
+        per_step = len(dev_probs)
+        value = args.steps * per_step * world / (ms / 1e3)
 
-        # Roofline of the dominant kernel pair: (N + delta I) v, A^T pass + A pass.
-        D = torch.rand(n, dtype=torch.float64, device=dev) + 0.5
-        v = torch.randn(m, dtype=torch.float64, device=dev)
-        out = torch.empty_like(v)
-        for _ in range(3):
-            nys.nys_normal_matvec(h, A, D, 1e-3, v, out)
-        reps = 20
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(reps):
-            nys.nys_normal_matvec(h, A, D, 1e-3, v, out)
-        f1.record(stream)
-        torch.cuda.synchronize(dev)
-        op_s = f0.elapsed_time(f1) / reps / 1e3
-        flops = 4.0 * m * n                      # 2 FMA per element of A per operator application
-        bytes_alg = 2.0 * m * n * 8 + 8.0 * (3 * m + 2 * n)
-        peak = fp64_alu_peak_tflops()
-        tr = traffic_record("gemv_f64.cu")
-        roofline = {"bound": "alu", "achieved": flops / op_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": flops / op_s / 1e12 / peak,
-                    "traffic": (tr["bytes_per_launch"] * (m * n) / tr["elements"]) if tr else None,
-                    "kernel": "normal-equations operator (k_atv_partial + k_atv_reduce + k_av), FP64",
-                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
-                    "hbm_gbs": bytes_alg / op_s / 1e9, "op_ms": op_s * 1e3,
-                    "algorithmic_flops": flops, "algorithmic_bytes": bytes_alg}
+        # ---- roofline of the dominant kernel (the normal-equations operator)
+        A0 = dev_probs[0][0]
+        m0, n0 = A0.shape
+        hbm_peak, bf16_peak, peak_src = measured_peaks()
+        if form == "bf16":
+            # BF16 operator: A^T pass over the BF16 transpose + A pass, FP32 accumulation
+            flops = 4.0 * m0 * n0
+            bytes_alg = 2.0 * m0 * n0 * 2 + 4.0 * (3 * m0 + 2 * n0)
+            op_s = time_lp_operator(nys, h, A0, stream)
+            roofline = {"bound": "hbm", "achieved": bytes_alg / op_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": bytes_alg / op_s / 1e9 / hbm_peak, "traffic": None,
+                        "kernel": "BF16 normal-equations operator (k_rows<bf16> over A^T and A)",
+                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})", "op_ms": op_s * 1e3,
+                        "algorithmic_bytes": bytes_alg}
+        else:
+            flops = 4.0 * m0 * n0
+            bytes_alg = 2.0 * m0 * n0 * 8 + 8.0 * (3 * m0 + 2 * n0)
+            D = torch.rand(n0, dtype=torch.float64, device=dev) + 0.5
+            v = torch.randn(m0, dtype=torch.float64, device=dev)
+            out = torch.empty_like(v)
+            for _ in range(3):
+                nys.nys_normal_matvec(h, A0, D, 1e-3, v, out)
+            reps = 50
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(reps):
+                nys.nys_normal_matvec(h, A0, D, 1e-3, v, out)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            op_s = f0.elapsed_time(f1) / reps / 1e3
+            peak = fp64_alu_peak_tflops()
+            tr = traffic_record("gemv_f64.cu", "fp64_operator")
+            roofline = {"bound": "alu", "achieved": flops / op_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": flops / op_s / 1e12 / peak,
+                        "traffic": (tr["bytes_per_element"] * m0 * n0) if tr else None,
+                        "kernel": "FP64 normal-equations operator (k_atv_partial + k_atv_reduce + k_av)",
+                        "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
+                        "hbm_gbs": bytes_alg / op_s / 1e9, "op_ms": op_s * 1e3,
+                        "algorithmic_flops": flops, "algorithmic_bytes": bytes_alg}
 
-        # e2e through the C ABI with pinned host buffers
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        hA, hb, hc, hq, hx0, hy0, hz0 = (pin(vv) for vv in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0))
-        nys.nys_solve(h, hA, hb, hc, hq, hx0, hy0, hz0)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            nys.nys_solve(h, hA, hb, hc, hq, hx0, hy0, hz0)
-        torch.cuda.synchronize(dev)
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            e2e_s = float(te[0])
-        h2d = 8 * (m * n + m + 3 * n + n + m + n)
-        d2h = 8 * (2 * n + m)
+        # ---- e2e: the same solves through the C ABI from pinned host buffers
+        e2e = None
+        if form in ("fp64", "bf16"):
+            pin = lambda t: t.detach().cpu().pin_memory()
+            hp = [tuple(pin(t) for t in pr[:7]) for pr in dev_probs]
+            nys.nys_solve(h, *hp[0])
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                for pr in hp:
+                    nys.nys_solve(h, *pr)
+            e2e_s = time.perf_counter() - t0
+            if world > 1:
+                te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+                dist.all_reduce(te, op=dist.ReduceOp.MAX)
+                e2e_s = float(te[0])
+            h2d = sum(sum(t.numel() * t.element_size() for t in pr) for pr in hp)
+            d2h = sum(8 * (2 * pr[0].shape[1] + pr[0].shape[0]) for pr in hp)
+            e2e = {"value": args.steps * per_step * world / e2e_s, "unit": "QP solves/s",
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        else:
+            e2e = {"value": None, "unit": "QP solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                   "note": "batch/diff workloads take device tensors only"}
 
-    last = infos[-1]
+        fp64_cmp = None
+        if form == "bf16" and args.compare_fp64:
+            A64 = dev_probs[0][0].double()
+            h64 = nys.Handle(m0, n0, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream)
+            t0 = time.perf_counter()
+            _, _, _, i64 = nys.nys_solve(h64, A64, *dev_probs[0][1:7], check=False)
+            torch.cuda.synchronize(dev)
+            t64 = time.perf_counter() - t0
+            fp64_cmp = {"value": 1.0 / t64, "unit": "QP solves/s", "status": i64["status"],
+                        "ipm_iters": i64["ipm_iters"], "pcg_iters": i64["pcg_iters_total"]}
+            h64.close()
+            del A64
+
+    last = runs[0]
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(qp, w, last["ipm_iters"], last["pcg_iters_total"], seed)
+            probs = []
+            if host_probs is not None:
+                for qp, pr in zip(host_probs[:4], dev_probs[:4]):
+                    probs.append(dict(A64=qp.A, b=qp.b, c=qp.c, q=qp.q, x0=qp.x0, y0=qp.y0, z0=qp.z0, ell=pr[7]))
+            else:
+                pr = dev_probs[0]
+                probs.append(dict(A64=pr[0].double().cpu().numpy(), b=pr[1].cpu().numpy(), c=pr[2].cpu().numpy(),
+                                  q=pr[3].cpu().numpy(), x0=pr[4].cpu().numpy(), y0=pr[5].cpu().numpy(),
+                                  z0=pr[6].cpu().numpy(), ell=pr[7]))
+            cpu = cpu_baseline(probs, w, runs, seed)
         line = {
             "metric": "QP solves/s to KKT tol", "value": value, "unit": "QP solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "m": m, "n": n, "ell": w["ell"],
-                       "tol": w["tol"], "form": "fp64", "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 (A = {m * n * 8 / 1e6:.0f} MB)" if m * n * 8 > 129e6
-                       else "A fits in L2 (no flush)"},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": args.steps * world / e2e_s, "unit": "QP solves/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "clocks": clocks, "gpu_launches": launches,
-            "solve": {"status": last["status"], "ipm_iters": last["ipm_iters"],
-                      "pcg_iters": last["pcg_iters_total"], "rel_primal": last["rel_primal"],
-                      "rel_dual": last["rel_dual"], "mu": last["mu"], "rel_gap": last["rel_gap"]},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16": "bf16", "batch": "f64", "diff": "f64"}[form], "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
+                       "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6
+                       else f"A = {a_bytes / 1e6:.1f} MB fits in L2 (no flush; latency-bound)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "solve": {"status": max(r["status"] for r in runs), "ipm_iters": last["ipm_iters"],
+                      "pcg_iters": last["pcg_iters_total"], "refine_steps": last["refine_steps"],
+                      "rel_primal": max(r["rel_primal"] for r in runs), "rel_dual": max(r["rel_dual"] for r in runs),
+                      "mu": max(r["mu"] for r in runs)},
         }
+        if fp64_cmp is not None:
+            line["fp64_form_same_qp"] = fp64_cmp
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def time_lp_operator(nys, h, A32, stream):
+    """Average duration of the precision form's BF16 operator pair (A^T pass
+    over the BF16 transpose, then the A pass), CUDA events on `stream`."""
+    import torch
+    dev = A32.device
+    m, n = A32.shape
+    Ab = A32.to(torch.bfloat16)
+    AbT = A32.T.contiguous().to(torch.bfloat16)
+    D = torch.rand(n, dtype=torch.float64, device=dev) + 0.5
+    v = torch.randn(m, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    for _ in range(3):
+        nys.nys_normal_matvec_lp(h, Ab, AbT, D, 1e-3, v, out)
+    reps = 20
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(reps):
+        nys.nys_normal_matvec_lp(h, Ab, AbT, D, 1e-3, v, out)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    del Ab, AbT
+    return f0.elapsed_time(f1) / reps / 1e3
 
 
 if __name__ == "__main__":

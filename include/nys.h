@@ -82,6 +82,8 @@ typedef struct {
     int host;
     const double *lam0, *zeta0;   /* m, n, or NULL                                    */
     int k0;
+    int ell;                      /* sketch size for this problem (0 = the handle's), */
+                                  /* clamped to the handle's ell and to m             */
 } nys_problem;
 
 /* Result.  x, y, z are caller-allocated outputs (n, m, n) in the same memory
@@ -122,7 +124,33 @@ int nys_create(nys_handle* h, const nys_options* opt, int max_m, int max_n, int 
  * also stored in r->status. */
 int nys_solve(nys_handle h, const nys_problem* p, nys_result* r);
 
+/* Solve `count` independent QPs (the batching form), each exactly as
+ * nys_solve would, with up to max_batch of them in flight at once: a pool of
+ * host worker threads, each owning a private solver (workspace, CUDA stream,
+ * cached PCG graph) sized for the handle's max_m x max_n, pulls problems from
+ * a shared queue.  p[i] and r[i] follow nys_solve's conventions (device or
+ * host memory per problem).  The handle must have been created with
+ * max_batch >= 1.  Returns the worst status (negative errors first); each
+ * r[i].status holds its own.  All work is complete on return. */
+int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result* r);
+
 int nys_destroy(nys_handle h);
+
+/* Gradients of a loss L(x*) through the solutions of `count` solved QPs (the
+ * differentiation form).  At each final iterate the transposed regularised
+ * KKT system J^T lam = (dL/dx, 0, 0), J the Newton matrix of Eq. Newton at
+ * the final (x, z, rho, delta), is reduced exactly like Eq. normal-eq:
+ *   (A D A^T + delta I) lam2 = A D g,   lam1 = D (g - A^T lam2),
+ * solved by Nystrom PCG (a fresh sketch at the final D, relative tolerance
+ * eta), and
+ *   dL/dc = -lam1, dL/db = lam2, dL/dq = -lam1 .* x, dL/dA = y lam1^T - lam2 x^T.
+ * p[i], r[i]: the problems and results of the forward solves (device
+ * problems, FP64 A; x, y, z, rho, delta are read from r[i]).  Device arrays,
+ * QPs concatenated in order: dL_dx, dL_dc, dL_dq (sum n_i), dL_db (sum m_i),
+ * dL_dA (sum m_i n_i, each QP row-major m_i x n_i; FP64).  Any output may be
+ * NULL.  Returns the worst status over the QPs. */
+int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result* r, const double* dL_dx,
+                double eta, double* dL_dc, double* dL_db, double* dL_dq, double* dL_dA);
 
 /* Message of the last error recorded on h (static storage owned by h). */
 const char* nys_last_error(nys_handle h);
@@ -147,6 +175,16 @@ int nys_scaling(nys_handle h, int n, const double* x, const double* z, const dou
  * NYS_F64.  D: device n; v, out: device m (out must not alias v). */
 int nys_normal_matvec(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
                       const double* D, double delta, const double* v, double* out);
+
+/* The precision form's operator: out = A_r (D .* (A_r^T v)) + delta v with A_r
+ * stored in reduced precision (a_dtype NYS_BF16, or NYS_FP32) and given as two
+ * row-major copies, A (m x n, lda) and AT = A^T (n x m, ldat); products and
+ * sums in FP32 (Eq. normal-eq in the precision of the inner PCG solves).
+ * D, v, out: FP64 device.  The handle must be a precision-form handle
+ * (precision_mode 1); A and AT 16-byte aligned. */
+int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
+                         const void* AT, long long ldat, const double* D, double delta, const double* v,
+                         double* out);
 
 /* Omega_k (m x ell, leading dimension ld): entry (i, j) is the standard normal
  * deviate of Algorithm 1's first step drawn from the SplitMix64 stream of

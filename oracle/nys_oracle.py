@@ -323,12 +323,14 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     opt.delta0 carry the PMM parameters, and k0 is the index of the first IPM
     iteration (it selects Omega_k).  With record=True every trace entry also
     holds the state (x, y, z, lambda, zeta) at the top of its iteration.
-    READING (PEU, which the paper only cites): with
-    r_mu = |mu_{k+1} - mu_k| / max(mu_k, mu_{k+1}), if the primal infeasibility
-    ||b - A x|| fell to <= 0.95 of its previous value then lambda <- y and
-    delta <- max(floor, (1 - r_mu) delta), else delta <- max(floor,
-    (1 - 0.666 r_mu) delta); the same rule with the dual infeasibility
-    ||c + Q x - A^T y - z|| updates zeta <- x and rho."""
+    READING (PEU, which the paper only cites): after every iteration the
+    estimates follow the iterate, lambda <- y and zeta <- x (the proximal
+    centres are re-centred), and both regularisation parameters decay with
+    the relative change of mu: with r_mu = |mu_{k+1} - mu_k| / max(mu_k,
+    mu_{k+1}), rho <- max(floor, (1 - r_mu) rho), delta <- max(floor,
+    (1 - r_mu) delta).  (Keeping the estimates fixed until the infeasibility
+    drops by 5% never re-centres them from a feasible start, where the
+    infeasibility starts at zero, and costs 1.5-2x more IPM iterations.)"""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     x, y, z = x0.astype(np.float64).copy(), y0.astype(np.float64).copy(), z0.astype(np.float64).copy()
@@ -378,8 +380,6 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         dx, dy, dz = pred.dx + corr.dx, pred.dy + corr.dy, pred.dz + corr.dz
         alpha_p = step_length(x, dx)
         alpha_d = step_length(z, dz)
-        nrp_old = float(np.linalg.norm(b - Ax))
-        nrd_old = float(np.linalg.norm(c + q * x - Aty - z))
         x = x + alpha_p * dx
         y = y + alpha_d * dy
         z = z + alpha_d * dz
@@ -394,18 +394,10 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         trace.append(rec)
         # PEU (READING, see docstring).
         r_mu = abs(mu_new - mu) / max(mu, mu_new)
-        nrp_new = float(np.linalg.norm(b - A @ x))
-        nrd_new = float(np.linalg.norm(c + q * x - A.T @ y - z))
-        if nrp_new <= 0.95 * nrp_old:
-            lam_pmm = y.copy()
-            delta = max(opt.reg_floor, (1.0 - r_mu) * delta)
-        else:
-            delta = max(opt.reg_floor, (1.0 - 0.666 * r_mu) * delta)
-        if nrd_new <= 0.95 * nrd_old:
-            zeta = x.copy()
-            rho = max(opt.reg_floor, (1.0 - r_mu) * rho)
-        else:
-            rho = max(opt.reg_floor, (1.0 - 0.666 * r_mu) * rho)
+        lam_pmm = y.copy()
+        zeta = x.copy()
+        delta = max(opt.reg_floor, (1.0 - r_mu) * delta)
+        rho = max(opt.reg_floor, (1.0 - r_mu) * rho)
         mu = mu_new
         k += 1
     return Result(x=x, y=y, z=z, status=status, ipm_iters=k, pcg_iters=pcg_counts,

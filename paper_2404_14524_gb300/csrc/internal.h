@@ -206,6 +206,11 @@ cudaError_t add_dirs_f64(cudaStream_t st, int m, int n, const double* dxp, const
 // x += ap dx; z += ad dz (n);  y += ad dy (m)
 cudaError_t ipm_update_f64(cudaStream_t st, int m, int n, double ap, double ad, const double* dx,
                            const double* dy, const double* dz, double* x, double* y, double* z);
+// out = a .* b
+cudaError_t vmul_f64(cudaStream_t st, int len, const double* a, const double* b, double* out);
+// out[i, j] = alpha u_i v_j + beta w_i s_j, row-major m x n (FP32 or FP64 out)
+cudaError_t rank2_update(cudaStream_t st, int m, int n, double alpha, const double* u, const double* v, double beta,
+                         const double* w, const double* s, void* out, long long ldo, int out_f32);
 // out = a x + b y
 cudaError_t axpby_f64(cudaStream_t st, int len, double a, const double* x, double b, const double* y, double* out);
 // P (m x ell, column-major, FP64) rounded to BF16 in place; the BF16 copy goes

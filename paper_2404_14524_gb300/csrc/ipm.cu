@@ -187,7 +187,42 @@ __global__ void k_panel_f32_to_f64(int m, int ell, const float* __restrict__ src
   dst[(size_t)c * ldd + i] = (double)src[(size_t)c * lds + i];
 }
 
+__global__ void k_vmul(int len, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+  const int j = blockIdx.x * kNT + threadIdx.x;
+  if (j < len) out[j] = a[j] * b[j];
+}
+
+// out[i, j] = alpha u_i v_j + beta w_i s_j  (row-major m x n, leading dimension ldo)
+template <typename TO>
+__global__ void k_rank2(int m, int n, double alpha, const double* __restrict__ u, const double* __restrict__ v,
+                        double beta, const double* __restrict__ w, const double* __restrict__ s, TO* __restrict__ out,
+                        long long ldo) {
+  const int i = blockIdx.y;
+  const double ui = alpha * u[i], wi = beta * w[i];
+  TO* row = out + (long long)i * ldo;
+  for (int j = blockIdx.x * kNT + threadIdx.x; j < n; j += gridDim.x * kNT) row[j] = (TO)fma(ui, v[j], wi * s[j]);
+}
+
 }  // namespace
+
+cudaError_t vmul_f64(cudaStream_t st, int len, const double* a, const double* b, double* out) {
+  if (len <= 0) return cudaSuccess;
+  count_launches(1);
+  k_vmul<<<(len + kNT - 1) / kNT, kNT, 0, st>>>(len, a, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t rank2_update(cudaStream_t st, int m, int n, double alpha, const double* u, const double* v, double beta,
+                         const double* w, const double* s, void* out, long long ldo, int out_f32) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  int gx = (n + kNT - 1) / kNT;
+  if (gx > 8) gx = 8;
+  dim3 grid(gx, m);
+  count_launches(1);
+  if (out_f32) k_rank2<float><<<grid, kNT, 0, st>>>(m, n, alpha, u, v, beta, w, s, (float*)out, ldo);
+  else k_rank2<double><<<grid, kNT, 0, st>>>(m, n, alpha, u, v, beta, w, s, (double*)out, ldo);
+  return cudaGetLastError();
+}
 
 cudaError_t axpby_f64(cudaStream_t st, int len, double a, const double* x, double b, const double* y, double* out) {
   if (len <= 0) return cudaSuccess;

@@ -13,7 +13,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <atomic>
@@ -82,6 +84,10 @@ struct nys_solver {
   size_t upart_cap = 0;
   long long ld_b = 0, ld_bt = 0, ld_ft = 0, ld_om = 0, ld_tb = 0, ld_ff = 0;
   double *nd_m = nullptr, *u_n = nullptr, *rr = nullptr, *dyacc = nullptr, *ecorr = nullptr;
+  // batching form: worker solvers (created on first use), one per in-flight QP
+  int max_batch = 0;
+  std::vector<nys_solver*> workers;
+  std::vector<cudaStream_t> worker_streams;
 };
 
 namespace {
@@ -548,6 +554,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   h->ld = (int)align_up(max_m, 2);
   h->ld_t = (int)align_up(max_n, 2);
   h->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->max_batch = max_batch;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;
@@ -595,6 +602,8 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
 
 int nys_destroy(nys_handle h) {
   if (!h) return NYS_ERR_ARG;
+  for (nys_solver* w : h->workers) nys_destroy(w);
+  for (cudaStream_t s : h->worker_streams) cudaStreamDestroy(s);
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   drop_pcg_graph(h);
@@ -626,6 +635,22 @@ int nys_normal_matvec(nys_handle h, int m, int n, int a_dtype, const void* A, lo
   const double* Ad = static_cast<const double*>(A);
   CK(gemv_t_f64(h->st, m, n, Ad, lda, v, D, h->pw.t, h->split_buf, h->split_cap));
   CK(gemv_n_f64(h->st, m, n, Ad, lda, h->pw.t, delta, v, out));
+  return NYS_OK;
+}
+
+int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
+                         const void* AT, long long ldat, const double* D, double delta, const double* v,
+                         double* out) {
+  if (!h) return NYS_ERR_ARG;
+  if (!h->lp_arena) return fail(h, NYS_ERR_ARG, "nys_normal_matvec_lp: not a precision-form handle");
+  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || lda < n || ldat < m || !A || !AT || !D || !v ||
+      !out || out == v || (a_dtype != NYS_BF16 && a_dtype != NYS_F32))
+    return fail(h, NYS_ERR_ARG, "nys_normal_matvec_lp: bad argument");
+  const int bf = a_dtype == NYS_BF16;
+  CK(to_f32(h->st, n, (int)align_up(n, 8), D, nullptr, h->Df));
+  CK(to_f32(h->st, m, (int)align_up(m, 8), v, nullptr, h->xf));
+  CK(gemv_rows_lp(h->st, n, m, bf, AT, ldat, h->xf, h->Df, 0.0, nullptr, h->tf, 0));
+  CK(gemv_rows_lp(h->st, m, n, bf, A, lda, h->tf, nullptr, delta, v, out, 1));
   return NYS_OK;
 }
 
@@ -706,6 +731,98 @@ int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long
                 ld, lam, eta, max_iter, forced_iters, dx, dy, dz, iters);
 }
 
+int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result* r) {
+  if (!h) return NYS_ERR_ARG;
+  if (count < 0 || (count > 0 && (!p || !r))) return fail(h, NYS_ERR_ARG, "nys_solve_batched: bad argument");
+  if (h->max_batch < 1) return fail(h, NYS_ERR_ARG, "nys_solve_batched: handle created with max_batch = 0");
+  if (count == 0) return NYS_OK;
+  const int want = std::min(h->max_batch, count);
+  // the caller's stream must be drained before worker streams read its data
+  CK(cudaStreamSynchronize(h->st));
+  while ((int)h->workers.size() < want) {
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    nys_handle w = nullptr;
+    nys_options o = h->opt;
+    const int rc = nys_create(&w, &o, h->max_m, h->max_n, 0, s);
+    if (rc != NYS_OK) {
+      cudaStreamDestroy(s);
+      return fail(h, rc, "nys_solve_batched: cannot create worker solver %zu", h->workers.size());
+    }
+    h->workers.push_back(w);
+    h->worker_streams.push_back(s);
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  pool.reserve(want);
+  for (int t = 0; t < want; ++t) {
+    pool.emplace_back([&, t]() {
+      cudaSetDevice(h->device);
+      nys_solver* w = h->workers[t];
+      for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) nys_solve(w, &p[i], &r[i]);
+    });
+  }
+  for (auto& th : pool) th.join();
+  int worst_err = NYS_OK, worst_warn = NYS_OK;
+  for (int i = 0; i < count; ++i) {
+    if (r[i].status < worst_err) worst_err = r[i].status;
+    if (r[i].status > worst_warn) worst_warn = r[i].status;
+  }
+  if (worst_err < 0) return fail(h, worst_err, "nys_solve_batched: at least one problem failed");
+  return worst_warn;
+}
+
+int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result* r, const double* dL_dx,
+                double eta, double* dL_dc, double* dL_db, double* dL_dq, double* dL_dA) {
+  if (!h) return NYS_ERR_ARG;
+  if (count < 0 || (count > 0 && (!p || !r || !dL_dx)) || !(eta > 0.0))
+    return fail(h, NYS_ERR_ARG, "nys_adjoint: bad argument");
+  int worst = NYS_OK;
+  size_t on = 0, om = 0, omn = 0;
+  for (int i = 0; i < count; ++i) {
+    const nys_problem& P = p[i];
+    const nys_result& R = r[i];
+    const int m = P.m, n = P.n;
+    if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || P.a_dtype != NYS_F64 || P.host || !P.A || !P.q ||
+        P.lda < n || !R.x || !R.y || !R.z)
+      return fail(h, NYS_ERR_ARG, "nys_adjoint: problem %d is not a device FP64 problem of this handle", i);
+    const double* A = static_cast<const double*>(P.A);
+    const int ell = std::min(h->ell_cap, m);
+    const double* g = dL_dx + on;
+    CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
+    // final D and a fresh Nystrom factor of N at the solution
+    CK(scaling_f64(h->st, n, R.x, R.z, P.q, R.rho, h->D));
+    CK(gaussian_omega(h->st, h->opt.seed, R.ipm_iters + 1, m, ell, h->Om, h->ld));
+    CK(sketch_f64(h->st, m, n, A, P.lda, h->D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf,
+                  h->split_cap));
+    CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red, h->cw,
+                        h->num_sms));
+    // (N + delta I) lam2 = A (D .* g)
+    CK(vmul_f64(h->st, n, h->D, g, h->t_n));
+    CK(gemv_n_f64(h->st, m, n, A, P.lda, h->t_n, 0.0, nullptr, h->xi));
+    int it = 0;
+    int rc = run_pcg(h, m, n, A, P.lda, h->D, R.delta, ell, h->U, h->ld, h->lamh, h->xi, h->dyp, eta,
+                     h->opt.max_pcg_iter, -1, &it);
+    if (rc < 0) return rc;
+    if (rc > worst) worst = rc;
+    // -lam1 = D (A^T lam2 - g)
+    CK(gemv_t_f64(h->st, m, n, A, P.lda, h->dyp, nullptr, h->g_n, h->split_buf, h->split_cap));
+    CK(axpby_f64(h->st, n, 1.0, h->g_n, -1.0, g, h->dxp));
+    CK(vmul_f64(h->st, n, h->D, h->dxp, h->dxc));          // dxc = -lam1
+    if (dL_dc) CK(cudaMemcpyAsync(dL_dc + on, h->dxc, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    if (dL_db) CK(cudaMemcpyAsync(dL_db + om, h->dyp, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    if (dL_dq) CK(vmul_f64(h->st, n, h->dxc, R.x, dL_dq + on));
+    // dL/dA = y lam1^T - lam2 x^T = -(y (-lam1)^T) - lam2 x^T
+    if (dL_dA) CK(rank2_update(h->st, m, n, -1.0, R.y, h->dxc, -1.0, h->dyp, R.x, dL_dA + omn, n, 0));
+    rc = sync_scalars(h, 0);
+    if (rc != NYS_OK) return rc;
+    on += n;
+    om += m;
+    omn += (size_t)m * n;
+  }
+  return worst;
+}
+
 int nys_gemm_bf16(nys_handle h, int M, int N, int K, const void* A, long long lda, const void* B,
                   long long ldb, float* C, long long ldc) {
   if (!h) return NYS_ERR_ARG;
@@ -743,9 +860,9 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   const int lp = o.precision_mode == 1;
   if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n ||
       p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 ||
-      !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0)
+      !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0 || p->ell < 0)
     return fail(h, NYS_ERR_ARG, "nys_solve: bad problem (sizes, dtype for the precision mode, or null pointers)");
-  const int ell = std::min(h->ell_cap, m);
+  const int ell = std::min(std::min(h->ell_cap, m), p->ell > 0 ? p->ell : h->ell_cap);
   const long long lda = p->lda;
   r->status = NYS_OK;
   r->ipm_iters = 0;
@@ -802,7 +919,7 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   const double bnorm = std::sqrt(h->h_red[8]), cnorm = std::sqrt(h->h_red[9]);
 
   double rho = o.rho0, delta = o.delta0;
-  double mu = 0.0, mu_prev = 0.0, nrp_prev = 0.0, nrd_prev = 0.0;
+  double mu = 0.0, mu_prev = 0.0;
   double rel_p = 0.0, rel_d = 0.0;
   int forced_idx = 0;
   int warn = NYS_OK;
@@ -835,24 +952,17 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
     rel_p = nrp / (1.0 + bnorm);
     rel_d = nrd / (1.0 + cnorm);
     if (k > 0) {
-      // PMM parameter update (reading of PEU: see the oracle's docstring).
+      // PMM parameter update (reading of PEU): re-centre the proximal
+      // estimates on the iterate and decay rho, delta with the change of mu.
       const double den = std::max(mu_prev, mu);
       const double r_mu = den > 0.0 ? std::fabs(mu - mu_prev) / den : 0.0;
-      if (nrp <= 0.95 * nrp_prev) {
-        CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
-        delta = std::max(o.reg_floor, (1.0 - r_mu) * delta);
-      } else {
-        delta = std::max(o.reg_floor, (1.0 - 0.666 * r_mu) * delta);
-      }
-      if (nrd <= 0.95 * nrd_prev) {
-        CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-        rho = std::max(o.reg_floor, (1.0 - r_mu) * rho);
-      } else {
-        rho = std::max(o.reg_floor, (1.0 - 0.666 * r_mu) * rho);
-      }
+      CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      delta = std::max(o.reg_floor, (1.0 - r_mu) * delta);
+      rho = std::max(o.reg_floor, (1.0 - r_mu) * rho);
       // predictor right-hand sides with the updated PMM parameters
       CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
-                             rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
+                           rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
     }
     // Termination (reading of TC: relative infeasibilities and mu).
     if (o.forced_ipm_iters >= 0) {
@@ -917,8 +1027,6 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
     const double ad = 0.995 * std::min(1.0, h->h_red[1]);
     CK(ipm_update_f64(h->st, m, n, ap, ad, h->dxc, h->dyc, h->dzc, h->x, h->y, h->z));
     mu_prev = mu;
-    nrp_prev = nrp;
-    nrd_prev = nrd;
     ++k;
   }
 

@@ -33,7 +33,7 @@ constexpr int kBK = 64;         // K per stage: 64 BF16 = 128 bytes = one swizzl
 constexpr int kUmmaK = 16;      // K per tcgen05.mma for kind::f16
 constexpr int kThreads = 128;
 constexpr unsigned kTmemCols = 512;
-constexpr unsigned long long kSpinLimit = 1ull << 26;
+constexpr unsigned long long kSpinLimit = 1ull << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));

@@ -55,7 +55,7 @@ class Problem(ctypes.Structure):
                 ("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("q", ctypes.c_void_p),
                 ("x0", ctypes.c_void_p), ("y0", ctypes.c_void_p), ("z0", ctypes.c_void_p),
                 ("host", ctypes.c_int), ("lam0", ctypes.c_void_p), ("zeta0", ctypes.c_void_p),
-                ("k0", ctypes.c_int)]
+                ("k0", ctypes.c_int), ("ell", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -85,6 +85,7 @@ _SIGS = {
     "nys_kernel_launches": (ctypes.c_ulonglong, []),
     "nys_scaling": (_I, [_P, _I, _P, _P, _P, _D, _P]),
     "nys_normal_matvec": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _P, _P]),
+    "nys_normal_matvec_lp": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _D, _P, _P]),
     "nys_gaussian": (_I, [_P, ctypes.c_ulonglong, _I, _I, _I, _P, _I]),
     "nys_sketch": (_I, [_P, _I, _I, _I, _P, _LL, _P, _I, _P, _P, _I]),
     "nys_nystrom": (_I, [_P, _I, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_D)]),
@@ -95,6 +96,8 @@ _SIGS = {
                         _I, _I, _P, _P, _P, ctypes.POINTER(_I)]),
     "nys_step_length": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
     "nys_gemm_bf16": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL]),
+    "nys_solve_batched": (_I, [_P, _I, ctypes.POINTER(Problem), ctypes.POINTER(Result)]),
+    "nys_adjoint": (_I, [_P, _I, ctypes.POINTER(Problem), ctypes.POINTER(Result), _P, _D, _P, _P, _P, _P]),
 }
 
 
@@ -217,6 +220,17 @@ def nys_normal_matvec(h: Handle, A, D, delta: float, v, out=None):
     h.check(lib().nys_normal_matvec(h.h, m, n, NYS_F64, _ptr(_f64(A, "A")), A.stride(0),
                                     _ptr(_f64(D, "D")), float(delta), _ptr(_f64(v, "v")),
                                     _ptr(_f64(out, "out"))))
+    return out
+
+
+def nys_normal_matvec_lp(h: Handle, A, AT, D, delta: float, v, out=None):
+    """Precision-form operator with reduced-precision copies A (m x n) and
+    AT (n x m), torch.bfloat16 or float32, row-major."""
+    m, n = A.shape
+    dt = {torch.bfloat16: NYS_BF16, torch.float32: NYS_F32}[A.dtype]
+    out = torch.empty_like(v) if out is None else out
+    h.check(lib().nys_normal_matvec_lp(h.h, m, n, dt, _ptr(A), A.stride(0), _ptr(AT), AT.stride(0),
+                                       _ptr(_f64(D, "D")), float(delta), _ptr(_f64(v, "v")), _ptr(_f64(out, "out"))))
     return out
 
 
@@ -350,3 +364,78 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     if want_pmm:
         info["lam"], info["zeta"] = lam, zeta
     return x, y, z, info
+
+
+def nys_adjoint(h: Handle, A, q, x, y, z, info, dL_dx, eta: float = 1e-12):
+    """Gradients of L(x*) for one solved QP (device FP64 tensors; `info` is the
+    dict returned by nys_solve).  Returns dict(c=..., b=..., q=..., A=...)."""
+    m, n = A.shape
+    _f64(A, "A", A.device)
+    p = Problem(m=m, n=n, a_dtype=NYS_F64, A=A.data_ptr(), lda=A.stride(0), q=_f64(q, "q").data_ptr(), host=0)
+    r = Result(x=_f64(x, "x").data_ptr(), y=_f64(y, "y").data_ptr(), z=_f64(z, "z").data_ptr(),
+               rho=info["rho"], delta=info["delta"], ipm_iters=info["ipm_iters"])
+    gc, gq = torch.empty(n, dtype=torch.float64, device=A.device), torch.empty(n, dtype=torch.float64, device=A.device)
+    gb = torch.empty(m, dtype=torch.float64, device=A.device)
+    gA = torch.empty(m, n, dtype=torch.float64, device=A.device)
+    rc = lib().nys_adjoint(h.h, 1, ctypes.byref(p), ctypes.byref(r), _ptr(_f64(dL_dx, "dL_dx")), float(eta),
+                           _ptr(gc), _ptr(gb), _ptr(gq), _ptr(gA))
+    h.check(rc)
+    return {"c": gc, "b": gb, "q": gq, "A": gA}
+
+
+class NysQPFunction(torch.autograd.Function):
+    """x* = argmin of the separable QP (P) as a differentiable function of
+    (A, b, c, q).  Forward: nys_solve; backward: nys_adjoint (transposed-KKT
+    solve by Nystrom PCG).  A FP32 input is solved in FP64 and its gradient
+    returned in FP32."""
+
+    @staticmethod
+    def forward(ctx, A, b, c, q, x0, y0, z0, handle, eta):
+        A64 = A.double().contiguous()
+        x, y, z, info = nys_solve(handle, A64, b, c, q, x0, y0, z0)
+        ctx.save_for_backward(A64, q, x, y, z)
+        ctx.info, ctx.handle, ctx.eta, ctx.a_dtype = info, handle, eta, A.dtype
+        ctx.mark_non_differentiable(y, z)
+        return x, y, z
+
+    @staticmethod
+    def backward(ctx, gx, gy, gz):
+        A64, q, x, y, z = ctx.saved_tensors
+        g = nys_adjoint(ctx.handle, A64, q, x, y, z, ctx.info, gx.contiguous(), ctx.eta)
+        return g["A"].to(ctx.a_dtype), g["b"], g["c"], g["q"], None, None, None, None, None
+
+
+def qp_solve(A, b, c, q, x0, y0, z0, handle, eta: float = 1e-12):
+    """Differentiable solve: returns (x, y, z); gradients flow to A, b, c, q through x."""
+    return NysQPFunction.apply(A, b, c, q, x0, y0, z0, handle, eta)
+
+
+def nys_solve_batched(h: Handle, problems, check: bool = True):
+    """Solve a list of QPs [(A, b, c, q, x0, y0, z0[, ell]), ...] (device
+    tensors; optional per-problem sketch size) in one call; the handle must
+    have max_batch >= 1.  Returns a list of (x, y, z, info)."""
+    k = len(problems)
+    P = (Problem * k)()
+    R = (Result * k)()
+    outs = []
+    for i, pr in enumerate(problems):
+        A, b, c, q, x0, y0, z0 = pr[:7]
+        ell_i = int(pr[7]) if len(pr) > 7 else 0
+        m, n = A.shape
+        a_dtype = NYS_F32 if A.dtype == torch.float32 else NYS_F64
+        x = torch.empty(n, dtype=torch.float64, device=A.device)
+        y = torch.empty(m, dtype=torch.float64, device=A.device)
+        z = torch.empty(n, dtype=torch.float64, device=A.device)
+        P[i] = Problem(m=m, n=n, a_dtype=a_dtype, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(), c=c.data_ptr(),
+                       q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(), z0=z0.data_ptr(), host=0, ell=ell_i)
+        R[i] = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr())
+        outs.append((x, y, z))
+    rc = lib().nys_solve_batched(h.h, k, P, R)
+    if check:
+        h.check(rc)
+    res = []
+    for i, (x, y, z) in enumerate(outs):
+        info = {f: getattr(R[i], f) for f in ("status", "ipm_iters", "pcg_iters_total", "refine_steps", "rel_primal",
+                                              "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds")}
+        res.append((x, y, z, info))
+    return res

@@ -174,3 +174,39 @@ def workload_diff(seed: int = 1239, count: int = 64, m: int = 512, n: int = 2048
     qps = [gaussian_qp(seed * 1000 + t, m, n, "uniform_0.1") for t in range(count)]
     targets = [rng.uniform(0.0, 1.0, n) for _ in range(count)]
     return qps, targets
+
+
+def spectral_qp_device(seed: int, m: int, n: int, sigma_kind: str, q_kind: str = "uniform",
+                       device="cuda", dtype=None):
+    """Large-scale variant of `spectral_qp` generated on the GPU with torch
+    (Haar factors from a QR of a Gaussian on the device).  A is returned in
+    `dtype` (float32 by default: the FP32 matrix then defines the problem) and
+    the feasible start is built from that stored A in FP64.  Returns torch
+    tensors on `device`: A, b, c, q, x0, y0, z0."""
+    import torch
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device).manual_seed(seed)
+    i = torch.arange(1, m + 1, dtype=torch.float64, device=device)
+    sigma = {"inv": 1.0 / i, "pow0.8": i ** -0.8, "exp200": torch.exp(-i / 200.0) + 1e-3}[sigma_kind]
+    work = torch.float32
+    u, ru = torch.linalg.qr(torch.randn(m, m, generator=g, device=device, dtype=work))
+    u = u * torch.where(torch.diagonal(ru) < 0, -1.0, 1.0)
+    v, rv = torch.linalg.qr(torch.randn(n, m, generator=g, device=device, dtype=work))
+    v = v * torch.where(torch.diagonal(rv) < 0, -1.0, 1.0)
+    A = ((u * sigma.to(work)) @ v.T).to(dtype).contiguous()
+    del u, v, ru, rv
+    gq = torch.rand(n, generator=g, device=device, dtype=torch.float64)
+    if q_kind == "half_zero":
+        gq[torch.randperm(n, generator=g, device=device)[: n // 2]] = 0.0
+    elif q_kind == "uniform_0.1":
+        gq = 0.1 + 0.9 * gq
+    elif q_kind == "zero":
+        gq = torch.zeros_like(gq)
+    x0 = 0.5 + torch.rand(n, generator=g, device=device, dtype=torch.float64)
+    y0 = torch.randn(m, generator=g, device=device, dtype=torch.float64)
+    z0 = torch.rand(n, generator=g, device=device, dtype=torch.float64).clamp(min=Z0_FLOOR)
+    A64 = A.double()
+    b = A64 @ x0
+    c = A64.T @ y0 + z0 - gq * x0
+    del A64
+    return A, b, c, gq, x0, y0, z0
