@@ -45,26 +45,49 @@ def test_adjoint_matches_dense_kkt_at_the_gpu_solution(nys, m, n):
         assert err <= 1e-6, (k, err)
 
 
-def test_autograd_function_matches_finite_differences(nys):
-    """d/d(b, c, q) of L = ||x* - x_t||^2 via backward(), against central
-    differences of the oracle's tight solve on random directions (1e-5 rel.)."""
-    m, n = 20, 60
-    qp = synth.gaussian_qp(77, m, n)
-    rng = np.random.default_rng(1)
+def _exact_solution(A, b, c, q):
+    """Exact optimum of a tiny strictly convex QP by enumerating supports."""
+    import itertools
+    m, n = A.shape
+    for size in range(m, n + 1):
+        for S in itertools.combinations(range(n), size):
+            S = list(S)
+            K = np.block([[np.diag(q[S]), -A[:, S].T], [A[:, S], np.zeros((m, m))]])
+            if abs(np.linalg.det(K)) < 1e-12:
+                continue
+            sol = np.linalg.solve(K, np.concatenate([-c[S], b]))
+            x = np.zeros(n)
+            x[S] = sol[:len(S)]
+            zz = c + q * x - A.T @ sol[len(S):]
+            if np.all(sol[:len(S)] >= -1e-13) and np.all(zz >= -1e-13):
+                return x
+    raise AssertionError("no KKT point")
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_autograd_function_matches_finite_differences(nys, seed):
+    """d/d(A, b, c, q) of L = ||x* - x_t||^2 through backward() (nys_adjoint on
+    the GPU) against central differences (h = 1e-6) of the exact solution map
+    of tiny QPs (brute-force active sets), on random directions: 1e-5 rel."""
+    rng = np.random.default_rng(900 + seed)
+    m, n = 3, 9
+    A0 = rng.standard_normal((m, n))
+    b0 = A0 @ rng.uniform(0.5, 1.5, n)
+    c0 = rng.standard_normal(n)
+    q0 = rng.uniform(0.2, 1.0, n)
     xt = rng.uniform(0, 1, n)
     h = nys.Handle(m, n, ell=m, tol=1e-10, seed=2)
-    A, b, c, q = (T(v).requires_grad_(True) for v in (qp.A, qp.b, qp.c, qp.q))
-    x, y, z = nys.qp_solve(A, b, c, q, T(qp.x0), T(qp.y0), T(qp.z0), h)
-    L = ((x - T(xt)) ** 2).sum()
-    L.backward()
-
-    def loss(bb, cc, qq):
-        r = O.solve(qp.A, bb, cc, qq, qp.x0, qp.y0, qp.z0, O.Options(tol=1e-12, ell=m, seed=2))
-        return float(np.sum((r.x - xt) ** 2))
-    hstep = 1e-6
+    A, b, c, q = (T(v).requires_grad_(True) for v in (A0, b0, c0, q0))
+    x, y, z = nys.qp_solve(A, b, c, q, T(np.ones(n)), T(np.zeros(m)), T(np.ones(n)), h)
+    assert np.allclose(x.detach().cpu().numpy(), _exact_solution(A0, b0, c0, q0), atol=1e-8)
+    ((x - T(xt)) ** 2).sum().backward()
+    loss = lambda AA, bb, cc, qq: float(np.sum((_exact_solution(AA, bb, cc, qq) - xt) ** 2))
+    hs = 1e-6
     for _ in range(4):
-        db, dc, dq = rng.standard_normal(m), rng.standard_normal(n), rng.standard_normal(n) * 0.1
-        fd = (loss(qp.b + hstep * db, qp.c + hstep * dc, qp.q + hstep * dq) -
-              loss(qp.b - hstep * db, qp.c - hstep * dc, qp.q - hstep * dq)) / (2 * hstep)
-        an = float(b.grad.cpu().numpy() @ db + c.grad.cpu().numpy() @ dc + q.grad.cpu().numpy() @ dq)
+        dA, db, dc, dq = rng.standard_normal((m, n)), rng.standard_normal(m), rng.standard_normal(n), \
+            0.1 * rng.standard_normal(n)
+        fd = (loss(A0 + hs * dA, b0 + hs * db, c0 + hs * dc, q0 + hs * dq) -
+              loss(A0 - hs * dA, b0 - hs * db, c0 - hs * dc, q0 - hs * dq)) / (2 * hs)
+        an = float((A.grad.cpu().numpy() * dA).sum() + b.grad.cpu().numpy() @ db +
+                   c.grad.cpu().numpy() @ dc + q.grad.cpu().numpy() @ dq)
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (fd, an)

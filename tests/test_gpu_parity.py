@@ -270,13 +270,14 @@ def small_run():
     return qp, ref
 
 
-@pytest.mark.parametrize("k", [0, 1, 2, 5, 9, 13, 18, 22, 26, 27])
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 9, 13, -4, -3, -2, -1])
 def test_single_ipm_step_matches_oracle(nys, small_run, k):
     """One IPM iteration (sketch, core, two PCG solves, steps, PEU) resumed on
     the GPU from the oracle's state k, with the oracle's PCG counts: the next
     iterate must agree to 1e-9 relative, or to 100x the oracle's own response
     to a 2e-16 perturbation of Omega_k where that floor is higher."""
     qp, ref = small_run
+    k = k % len(ref.trace)
     t = ref.trace[k]
     x, y, z, lam, zeta = t.state
     forced = [t.pcg_pred, t.pcg_corr]
