@@ -263,7 +263,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision workloads: also time one FP64-form solve of the same QP")
+    ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm"],
+                    help="run only this kernel --reps times on an m x n (x ell) case (for ncu captures)")
+    ap.add_argument("--m", type=int, default=5000)
+    ap.add_argument("--n", type=int, default=20000)
+    ap.add_argument("--ell", type=int, default=400)
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
+    if args.profile_kernel:
+        profile_kernel(args)
+        return
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -463,6 +472,50 @@ def main():
     h.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def profile_kernel(args):
+    """A few launches of one kernel on a bounded case, CUDA-event timed."""
+    import torch
+    from paper_2404_14524_gb300 import build
+    build.build()
+    from paper_2404_14524_gb300 import nys
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    m, n, reps = args.m, args.n, args.reps
+    if args.profile_kernel == "f64_operator":
+        A = torch.randn(m, n, generator=g, device=dev, dtype=torch.float64)
+        h = nys.Handle(m, n, ell=8)
+        D = torch.rand(n, generator=g, device=dev, dtype=torch.float64) + 0.5
+        v = torch.randn(m, generator=g, device=dev, dtype=torch.float64)
+        run = lambda: nys.nys_normal_matvec(h, A, D, 1e-3, v)
+        work = {"bytes": 16.0 * m * n, "flops": 4.0 * m * n}
+    elif args.profile_kernel == "bf16_operator":
+        A = (torch.randn(m, n, generator=g, device=dev) / 100).to(torch.bfloat16)
+        AT = A.T.contiguous()
+        h = nys.Handle(m, n, ell=8, precision_mode=1)
+        D = torch.rand(n, generator=g, device=dev, dtype=torch.float64) + 0.5
+        v = torch.randn(m, generator=g, device=dev, dtype=torch.float64)
+        run = lambda: nys.nys_normal_matvec_lp(h, A, AT, D, 1e-3, v)
+        work = {"bytes": 4.0 * m * n, "flops": 4.0 * m * n}
+    else:
+        ell = args.ell
+        A = (torch.randn(m, n, generator=g, device=dev) / 100).to(torch.bfloat16)
+        B = (torch.randn(ell, n, generator=g, device=dev) / 100).to(torch.bfloat16)
+        h = nys.Handle(m, 64, ell=ell, precision_mode=1)
+        run = lambda: nys.nys_gemm_bf16(h, A, B)
+        work = {"bytes": 2.0 * m * n, "flops": 2.0 * m * n * ell}
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / reps / 1e3
+    print(json.dumps({"kernel": args.profile_kernel, "m": m, "n": n, "reps": reps, "ms": sec * 1e3,
+                      "GB/s": work["bytes"] / sec / 1e9, "TFLOP/s": work["flops"] / sec / 1e12}), flush=True)
 
 
 def time_lp_operator(nys, h, A32, stream):

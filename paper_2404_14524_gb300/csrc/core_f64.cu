@@ -3,20 +3,26 @@
 //   C = chol(G) (upper, G = C^T C);  B = Y_nu C^{-1};  thin SVD of B;
 //   lam = max(0, Sigma^2 - nu) in descending order, U = left singular vectors.
 //
-// The thin SVD is a one-sided (Hestenes) Jacobi iteration on B itself, run
-// as one cooperative launch: each round rotates ell/2 disjoint column pairs
-// in parallel (one CTA per pair, round-robin ordering), with a bounded grid
-// barrier between rounds.  One-sided Jacobi orthogonalises the columns of B
-// directly, so small singular values keep their relative accuracy (no Gram
-// matrix, no squared condition number).  After convergence the column norms
-// are the singular values and the normalised columns the left singular
-// vectors.
+// The thin SVD is a one-sided (Hestenes) Jacobi iteration, run as one
+// cooperative launch: each round rotates ell/2 disjoint column pairs in
+// parallel (one CTA per pair, round-robin ordering), with a bounded grid
+// barrier between rounds.  One-sided Jacobi orthogonalises columns directly,
+// so small singular values keep their relative accuracy (no Gram matrix, no
+// squared condition number).  After convergence the column norms are the
+// singular values and the normalised columns the left singular vectors.
+// For ell <= 96 it runs on B itself; for larger ell on the triangular factor
+// R of B = Q R (shifted three-pass Cholesky QR), and B V = Q (R V).
 #include "common.cuh"
 #include "internal.h"
 
 namespace nys {
 
 namespace {
+
+// Above this sketch size the thin SVD goes through a QR of B first: one-sided
+// Jacobi directly on B costs ~3.5 m ell^2 DFMAs per sweep (8-10 sweeps),
+// the QR route ~4 m ell^2 DFMAs in total plus sweeps on an ell x ell matrix.
+constexpr int kJacobiDirectMaxEll = 96;
 
 __global__ void __launch_bounds__(kNT) k_frob(int m, int ell, const double* __restrict__ Y, int ld,
                                               double* sd, int* err, double* part, unsigned* cnt) {
@@ -173,6 +179,27 @@ __global__ void __launch_bounds__(kNT) k_jacobi(int m, int ell, double* B, int l
   if (blockIdx.x == 0 && tid == 0) *sweeps_out = max_sweeps + 1;   // not converged
 }
 
+// G[j][j] += f * trace(G)  (one CTA): the shift of the first Cholesky-QR pass.
+__global__ void __launch_bounds__(kNT) k_shift_trace(int ell, double* G, double f) {
+  __shared__ double sh[kWarps];
+  double v[1] = {0.0};
+  for (int j = threadIdx.x; j < ell; j += kNT) v[0] += G[(size_t)j * ell + j];
+  block_sum<kNT, 1>(v, sh);
+  const double s = f * v[0];
+  for (int j = threadIdx.x; j < ell; j += kNT) G[(size_t)j * ell + j] += s;
+}
+
+// out = Rn * Ra for upper-triangular ell x ell column-major matrices.
+__global__ void k_trmm_upper(int ell, const double* __restrict__ Rn, const double* __restrict__ Ra,
+                             double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (idx >= (long long)ell * ell) return;
+  const int i = (int)(idx % ell), j = (int)(idx / ell);
+  double s = 0.0;
+  for (int k = i; k <= j; ++k) s = fma(Rn[(size_t)k * ell + i], Ra[(size_t)j * ell + k], s);
+  out[(size_t)j * ell + i] = (i <= j) ? s : 0.0;
+}
+
 // Squared column norms, one block per column (fixed-order reduction).
 __global__ void __launch_bounds__(kNT) k_colnorm2(int m, const double* __restrict__ B, int ld,
                                                   double* __restrict__ sumsq) {
@@ -235,6 +262,38 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   k_chol<<<1, kNT, 0, st>>>(ell, cw.G, err);
   count_launches(1);
   k_trsm_rows<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, ell, cw.Ynu, ld, cw.G, err);
+  double* Bsv = cw.Ynu;           // matrix whose column norms / directions give U and Sigma
+  int jm = m, jld = ld;           // Jacobi problem: rows and leading dimension
+  double* Jmat = cw.Ynu;
+  if (ell > kJacobiDirectMaxEll) {
+    // Large ell: B = Q R by a shifted three-pass Cholesky QR (the first pass
+    // shifted by 1e-10 trace(B^T B) so it cannot break down), then the SVD of
+    // the small ell x ell R by one-sided Jacobi, W = R V, and B V = Q W.
+    for (int pass = 0; pass < 3; ++pass) {
+      e = gemm_f64(st, ell, ell, m, cw.Ynu, ld, 1, cw.Ynu, 1, ld, nullptr, cw.G, 1, ell, cw.split_buf,
+                   cw.split_cap);
+      if (e != cudaSuccess) return e;
+      if (pass == 0) {
+        count_launches(1);
+        k_shift_trace<<<1, kNT, 0, st>>>(ell, cw.G, 1e-10);
+      }
+      count_launches(1);
+      k_chol<<<1, kNT, 0, st>>>(ell, cw.G, err);
+      count_launches(1);
+      k_trsm_rows<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, ell, cw.Ynu, ld, cw.G, err);
+      const unsigned sb = (unsigned)(((long long)ell * ell + kNT - 1) / kNT);
+      if (pass == 0) {
+        cudaMemcpyAsync(cw.R, cw.G, sizeof(double) * ell * ell, cudaMemcpyDeviceToDevice, st);
+      } else {
+        count_launches(1);
+        k_trmm_upper<<<sb, kNT, 0, st>>>(ell, cw.G, cw.R, cw.Rt);
+        cudaMemcpyAsync(cw.R, cw.Rt, sizeof(double) * ell * ell, cudaMemcpyDeviceToDevice, st);
+      }
+    }
+    Jmat = cw.R;
+    jm = ell;
+    jld = ell;
+  }
   // one-sided Jacobi (cooperative)
   cudaMemsetAsync(cw.sweep_flags, 0, sizeof(int) * CoreWork::kMaxSweeps, st);
   cudaMemsetAsync(cw.bar, 0, 2 * sizeof(unsigned), st);
@@ -244,10 +303,10 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   const int cap = per_sm * num_sms;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  double tol = sqrt((double)m) * 0x1.0p-53;
+  double tol = sqrt((double)jm) * 0x1.0p-53;
   if (tol < 0x1.0p-52) tol = 0x1.0p-52;
-  int mm = m, ee = ell, ldd = ld, ms = CoreWork::kMaxSweeps;
-  double* Bp = cw.Ynu;
+  int mm = jm, ee = ell, ldd = jld, ms = CoreWork::kMaxSweeps;
+  double* Bp = Jmat;
   int* flags = cw.sweep_flags;
   unsigned* bar = cw.bar;
   int* sweeps = si + SI_SWEEPS;
@@ -255,12 +314,19 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   count_launches(1);
   e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kNT), args, 0, st);
   if (e != cudaSuccess) return e;
+  if (ell > kJacobiDirectMaxEll) {
+    // B V = Q W  (m x ell times ell x ell)
+    e = gemm_f64(st, m, ell, ell, cw.Ynu, 1, ld, cw.R, 1, ell, nullptr, cw.B2, 1, ld, cw.split_buf,
+                 cw.split_cap);
+    if (e != cudaSuccess) return e;
+    Bsv = cw.B2;
+  }
   count_launches(1);
-  k_colnorm2<<<ell, kNT, 0, st>>>(m, cw.Ynu, ld, cw.sumsq);
+  k_colnorm2<<<ell, kNT, 0, st>>>(m, Bsv, ld, cw.sumsq);
   count_launches(1);
   k_order<<<(ell + 127) / 128, 128, 0, st>>>(ell, cw.sumsq, sd, cw.perm, lam, err);
   count_launches(1);
-  k_normalise<<<eb, kNT, 0, st>>>(m, ell, cw.Ynu, ld, cw.sumsq, cw.perm, U, err);
+  k_normalise<<<eb, kNT, 0, st>>>(m, ell, Bsv, ld, cw.sumsq, cw.perm, U, err);
   return cudaGetLastError();
 }
 

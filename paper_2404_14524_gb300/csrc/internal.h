@@ -86,6 +86,9 @@ struct CoreWork {
   double* G;        // ell x ell      Omega^T Y_nu, then C (upper Cholesky factor)
   double* sumsq;    // ell            squared column norms of the converged B
   int* perm;        // ell            column of B that becomes column r of U
+  double* B2;       // m x ell (ld)   Q W for the QR route (large ell)
+  double* R;        // ell x ell      accumulated R of the QR passes, then W = R V
+  double* Rt;       // ell x ell      scratch product
   unsigned int* bar;  // 2 words      grid barrier
   int* sweep_flags;   // kMaxSweeps   rotation flags per Jacobi sweep
   double* split_buf;

@@ -149,6 +149,9 @@ size_t carve(nys_solver* h, char* base) {
   h->cw.perm = c.take<int>(L);
   h->cw.bar = c.take<unsigned>(2);
   h->cw.sweep_flags = c.take<int>(CoreWork::kMaxSweeps);
+  h->cw.B2 = c.take<double>(LD * L);
+  h->cw.R = c.take<double>(L * L);
+  h->cw.Rt = c.take<double>(L * L);
   h->cw.split_buf = h->split_buf;
   h->cw.split_cap = h->split_cap;
   h->pcg_x = c.take<double>(M);

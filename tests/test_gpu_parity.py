@@ -120,8 +120,11 @@ def _factor_pair(nys, m, n, ell, seed, rank=None, dscale=1.0):
     return h, A, D, Om, Fw, U.cpu().numpy().T, lam.cpu().numpy(), nu
 
 
-@pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (301, 450, 47), (64, 64, 64), (5, 9, 1)])
+@pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (301, 450, 47), (64, 64, 64), (5, 9, 1),
+                                     (600, 900, 120), (1000, 1500, 201)])
 def test_nystrom_factor_matches_oracle(nys, m, n, ell):
+    """Small ell: one-sided Jacobi on B; ell > 96: QR of B first (shifted
+    Cholesky QR3) and Jacobi on the ell x ell factor."""
     h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, m, n, ell, seed=m + ell)
     assert nu == Fw.nu
     assert np.all(np.diff(lam) <= 0) and np.all(lam >= 0)
