@@ -59,17 +59,21 @@ template <typename TA, typename TO, bool kVec>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_rows(int rows, int cols, const TA* __restrict__ A, long long lda, const float* __restrict__ x,
            const float* __restrict__ scale, double beta, const double* __restrict__ v, TO* __restrict__ out,
-           const int* __restrict__ skip, const double* __restrict__ beta_dev) {
+           const int* __restrict__ skip, const double* __restrict__ beta_dev, int cols_per_split,
+           double* __restrict__ part) {
   if (skip && *skip) return;
   if (beta_dev) beta = *beta_dev;
   const int lane = threadIdx.x & 31;
   const int r0 = (blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kRowsPerWarp;
   if (r0 >= rows) return;
+  // this block's column range (a multiple of 8 wide, except the last)
+  const int cb = blockIdx.y * cols_per_split;
+  const int ce = min(cols, cb + cols_per_split);
   float acc[kRowsPerWarp];
 #pragma unroll
   for (int i = 0; i < kRowsPerWarp; ++i) acc[i] = 0.0f;
-  const int cvec = kVec ? (cols / 8) * 8 : 0;
-  for (int c = lane * 8; c < cvec; c += 256) {
+  const int cvec = kVec ? cb + ((ce - cb) / 8) * 8 : cb;
+  for (int c = cb + lane * 8; c < cvec; c += 256) {
     float xv[8];
     load8(x + c, xv);
 #pragma unroll
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
       for (int j = 0; j < 8; ++j) acc[i] = fmaf(a[j], xv[j], acc[i]);
     }
   }
-  for (int c = cvec + lane; c < cols; c += 32) {
+  for (int c = cvec + lane; c < ce; c += 32) {
     const float xc = __ldg(x + c);
 #pragma unroll
     for (int i = 0; i < kRowsPerWarp; ++i) {
@@ -100,7 +104,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     for (int i = 1; i < kRowsPerWarp; ++i)
       if (lane == i) mine = acc[i];
     const int r = r0 + lane;
-    if (r < rows) {
+    if (r < rows && part) {
+      part[(size_t)blockIdx.y * rows + r] = (double)mine;
+    } else if (r < rows) {
       double val = (double)mine * (scale ? (double)scale[r] : 1.0);
       if (beta != 0.0) val = fma(beta, v[r], val);
       out[r] = (TO)val;
@@ -120,15 +126,20 @@ template <bool kVec>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_rows_ff(int rows, int cols, const float* __restrict__ A, long long lda, const float* __restrict__ xh,
               const float* __restrict__ xl, const double* __restrict__ scale, double beta,
-              const double* __restrict__ v, double* __restrict__ out) {
+              const double* __restrict__ v, double* __restrict__ out, const int* __restrict__ skip,
+              const double* __restrict__ beta_dev, int cols_per_split, double* __restrict__ part) {
+  if (skip && *skip) return;
+  if (beta_dev) beta = *beta_dev;
   const int lane = threadIdx.x & 31;
   const int r0 = (blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kRowsPerWarp;
   if (r0 >= rows) return;
+  const int cb = blockIdx.y * cols_per_split;
+  const int ce = min(cols, cb + cols_per_split);
   float sh[kRowsPerWarp], sl[kRowsPerWarp];
 #pragma unroll
   for (int i = 0; i < kRowsPerWarp; ++i) { sh[i] = 0.0f; sl[i] = 0.0f; }
-  const int cvec = kVec ? (cols / 8) * 8 : 0;
-  for (int c = lane * 8; c < cvec; c += 256) {
+  const int cvec = kVec ? cb + ((ce - cb) / 8) * 8 : cb;
+  for (int c = cb + lane * 8; c < cvec; c += 256) {
     float xa[8], xb[8];
     load8(xh + c, xa);
     load8(xl + c, xb);
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
       }
     }
   }
-  for (int c = cvec + lane; c < cols; c += 32) {
+  for (int c = cvec + lane; c < ce; c += 32) {
     const float xa = __ldg(xh + c), xb = __ldg(xl + c);
 #pragma unroll
     for (int i = 0; i < kRowsPerWarp; ++i) {
@@ -176,7 +187,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     for (int i = 1; i < kRowsPerWarp; ++i)
       if (lane == i) mine = tot[i];
     const int r = r0 + lane;
-    if (r < rows) {
+    if (r < rows && part) {
+      part[(size_t)blockIdx.y * rows + r] = mine;
+    } else if (r < rows) {
       double val = mine * (scale ? scale[r] : 1.0);
       if (beta != 0.0) val = fma(beta, v[r], val);
       out[r] = val;
@@ -184,9 +197,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
   }
 }
 
+// out[r] = scale[r] * sum_z part[z][r] + beta v[r]   (fixed order over z)
+template <typename TS, typename TO>
+__global__ void k_rows_finish(int rows, int splits, const double* __restrict__ part, const TS* __restrict__ scale,
+                              double beta, const double* __restrict__ v, TO* __restrict__ out,
+                              const int* __restrict__ skip, const double* __restrict__ beta_dev) {
+  if (skip && *skip) return;
+  if (beta_dev) beta = *beta_dev;
+  const int r = blockIdx.x * kNT + threadIdx.x;
+  if (r >= rows) return;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += part[(size_t)z * rows + r];
+  double val = s * (scale ? (double)scale[r] : 1.0);
+  if (beta != 0.0) val = fma(beta, v[r], val);
+  out[r] = (TO)val;
+}
+
 // x (FP64) -> hi, lo FP32 parts with x ~ hi + lo; padded entries are zero.
 __global__ void k_split_ff(int n, int npad, const double* __restrict__ x, const double* __restrict__ scale,
-                           float* __restrict__ hi, float* __restrict__ lo) {
+                           float* __restrict__ hi, float* __restrict__ lo, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int j = blockIdx.x * kNT + threadIdx.x;
   if (j >= npad) return;
   double v = 0.0;
@@ -237,52 +267,84 @@ int row_blocks(int rows) {
   return (rows + per - 1) / per;
 }
 
+// Column splits: enough blocks for ~4 per SM; every split at least 2048
+// columns wide; limited by the partial-sum scratch.
+int col_splits(int rows, int cols, size_t part_cap) {
+  const int rb = row_blocks(rows);
+  int s = (152 * 4 + rb - 1) / rb;
+  const int smax = cols / 2048;
+  if (s > smax) s = smax;
+  while (s > 1 && (size_t)s * rows > part_cap) --s;
+  return s < 1 ? 1 : s;
+}
+
 }  // namespace
 
 cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_bf16, const void* A, long long lda,
                          const float* x, const float* scale, double beta, const double* v, void* out,
-                         int out_f64, const int* skip, const double* beta_dev) {
+                         int out_f64, const int* skip, const double* beta_dev, double* part, size_t part_cap) {
   if (rows <= 0) return cudaSuccess;
-  const int b = row_blocks(rows);
+  const int S = part ? col_splits(rows, cols, part_cap) : 1;
+  const int cps = S > 1 ? ((cols + S - 1) / S + 7) / 8 * 8 : cols;
+  const int nsplit = (cols + cps - 1) / cps;
+  double* pp = nsplit > 1 ? part : nullptr;
+  dim3 grid(row_blocks(rows), nsplit);
   const int T = 32 * kWarpsPerBlock;
   count_launches(1);
   if (a_bf16) {
     const bool vec = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0);
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     if (out_f64) {
-      if (vec) k_rows<__nv_bfloat16, double, true><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev);
-      else k_rows<__nv_bfloat16, double, false><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev);
+      if (vec) k_rows<__nv_bfloat16, double, true><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev, cps, pp);
+      else k_rows<__nv_bfloat16, double, false><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev, cps, pp);
     } else {
-      if (vec) k_rows<__nv_bfloat16, float, true><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev);
-      else k_rows<__nv_bfloat16, float, false><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev);
+      if (vec) k_rows<__nv_bfloat16, float, true><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev, cps, pp);
+      else k_rows<__nv_bfloat16, float, false><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev, cps, pp);
     }
   } else {
     const bool vec = (lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0);
     const auto* a = static_cast<const float*>(A);
     if (out_f64) {
-      if (vec) k_rows<float, double, true><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev);
-      else k_rows<float, double, false><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev);
+      if (vec) k_rows<float, double, true><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev, cps, pp);
+      else k_rows<float, double, false><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev, cps, pp);
     } else {
-      if (vec) k_rows<float, float, true><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev);
-      else k_rows<float, float, false><<<b, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev);
+      if (vec) k_rows<float, float, true><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev, cps, pp);
+      else k_rows<float, float, false><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev, cps, pp);
     }
+  }
+  if (pp) {
+    count_launches(1);
+    const int fb = (rows + kNT - 1) / kNT;
+    if (out_f64) k_rows_finish<float, double><<<fb, kNT, 0, st>>>(rows, nsplit, pp, scale, beta, v, (double*)out, skip, beta_dev);
+    else k_rows_finish<float, float><<<fb, kNT, 0, st>>>(rows, nsplit, pp, scale, beta, v, (float*)out, skip, beta_dev);
   }
   return cudaGetLastError();
 }
 
 cudaError_t gemv_rows_ff(cudaStream_t st, int rows, int cols, const float* A, long long lda, const float* xh,
-                         const float* xl, const double* scale, double beta, const double* v, double* out) {
+                         const float* xl, const double* scale, double beta, const double* v, double* out,
+                         const int* skip, const double* beta_dev, double* part, size_t part_cap) {
   if (rows <= 0) return cudaSuccess;
+  const int S = part ? col_splits(rows, cols, part_cap) : 1;
+  const int cps = S > 1 ? ((cols + S - 1) / S + 7) / 8 * 8 : cols;
+  const int nsplit = (cols + cps - 1) / cps;
+  double* pp = nsplit > 1 ? part : nullptr;
+  dim3 grid(row_blocks(rows), nsplit);
   const bool vec = (lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0);
   count_launches(1);
-  if (vec) k_rows_ff<true><<<row_blocks(rows), 32 * kWarpsPerBlock, 0, st>>>(rows, cols, A, lda, xh, xl, scale, beta, v, out);
-  else k_rows_ff<false><<<row_blocks(rows), 32 * kWarpsPerBlock, 0, st>>>(rows, cols, A, lda, xh, xl, scale, beta, v, out);
+  if (vec) k_rows_ff<true><<<grid, 32 * kWarpsPerBlock, 0, st>>>(rows, cols, A, lda, xh, xl, scale, beta, v, out, skip, beta_dev, cps, pp);
+  else k_rows_ff<false><<<grid, 32 * kWarpsPerBlock, 0, st>>>(rows, cols, A, lda, xh, xl, scale, beta, v, out, skip, beta_dev, cps, pp);
+  if (pp) {
+    count_launches(1);
+    k_rows_finish<double, double><<<(rows + kNT - 1) / kNT, kNT, 0, st>>>(rows, nsplit, pp, scale, beta, v, out, skip, beta_dev);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t split_ff(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* hi, float* lo) {
+cudaError_t split_ff(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* hi, float* lo,
+                     const int* skip) {
   count_launches(1);
-  k_split_ff<<<(npad + kNT - 1) / kNT, kNT, 0, st>>>(n, npad, x, scale, hi, lo);
+  k_split_ff<<<(npad + kNT - 1) / kNT, kNT, 0, st>>>(n, npad, x, scale, hi, lo, skip);
   return cudaGetLastError();
 }
 

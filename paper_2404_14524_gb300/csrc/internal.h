@@ -104,14 +104,20 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
 // ---------------------------------------------------------------- precision-form GEMVs
 // out[r] = scale[r] * sum_c A[r, c] x[c] + beta v[r]; A BF16 (a_bf16) or FP32
 // row-major, x/scale FP32, FP32 accumulation; out FP64 (out_f64) or FP32.
+// With `part` (>= splits * rows doubles) short, wide matrices are split over
+// columns as well, with a fixed-order reduction of the partial sums.
 cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_bf16, const void* A, long long lda,
                          const float* x, const float* scale, double beta, const double* v, void* out,
-                         int out_f64, const int* skip = nullptr, const double* beta_dev = nullptr);
+                         int out_f64, const int* skip = nullptr, const double* beta_dev = nullptr,
+                         double* part = nullptr, size_t part_cap = 0);
 // FP32 A times x = xh + xl with float-float accumulation, FP64 out.
 cudaError_t gemv_rows_ff(cudaStream_t st, int rows, int cols, const float* A, long long lda, const float* xh,
-                         const float* xl, const double* scale, double beta, const double* v, double* out);
+                         const float* xl, const double* scale, double beta, const double* v, double* out,
+                         const int* skip = nullptr, const double* beta_dev = nullptr, double* part = nullptr,
+                         size_t part_cap = 0);
 // hi/lo FP32 split of scale .* x, zero padded to npad
-cudaError_t split_ff(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* hi, float* lo);
+cudaError_t split_ff(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* hi, float* lo,
+                     const int* skip = nullptr);
 cudaError_t to_f32(cudaStream_t st, int n, int npad, const double* x, const double* scale, float* y,
                    const int* skip = nullptr);
 // BF16 copy (dst, ldd), BF16 transpose (dstT, ldt) and FP32 transpose (dstTf,
@@ -160,6 +166,11 @@ cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, lo
 // A^T stored row-major in BF16 (bf16 = 1) or FP32, D in FP32; scratch xf
 // (ld_mpad floats, zero padded) and tf (n floats).
 struct LpOperator {
+  int ff;                           // 1: FP32 storage with float-float sums (A, AT FP32)
+  const double* D64;                // ff: FP64 D
+  double* t64;                      // ff: FP64 scratch of n for D .* (A^T p)
+  float *xh, *xl;                   // ff: hi/lo split scratch, max(m, n) padded
+  int ld_npad;
   int bf16;
   const void* A;  long long lda;    // m x n
   const void* AT; long long ldat;   // n x m
@@ -167,9 +178,19 @@ struct LpOperator {
   float* xf;
   float* tf;
   int ld_mpad;
+  double* part;                     // column-split partial sums
+  size_t part_cap;
 };
 cudaError_t pcg_iteration_lp(cudaStream_t st, int m, int n, const LpOperator& op, int ell,
                              const double* U, int ld, PcgWork w, double* sd, int* si, RedBuf red);
+// Whole PCG solve in one cooperative launch (small problems): same result
+// semantics as pcg_setup_f64 + pcg_iteration_f64 (solution in w.x, SI_ITERS,
+// SD_RR); part needs grid * (ell + 2) doubles, bar two zeroable words.
+bool pcg_persistent_fits(int m, int n, int ell);
+cudaError_t pcg_persistent_f64(cudaStream_t st, int m, int n, const double* A, long long lda, const double* D,
+                               double delta, int ell, const double* U, int ld, const double* lam, const double* xi,
+                               double eta, int max_iter, int forced, PcgWork w, double* part, size_t part_cap,
+                               unsigned* bar, double* sd, int* si, int num_sms);
 // Body-graph tail of a conditional while node: keep looping while !SI_DONE.
 cudaError_t pcg_loop_condition(cudaStream_t st, cudaGraphConditionalHandle cond, const int* si);
 

@@ -295,12 +295,28 @@ cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, lo
 cudaError_t pcg_iteration_lp(cudaStream_t st, int m, int n, const LpOperator& op, int ell,
                              const double* U, int ld, PcgWork w, double* sd, int* si, RedBuf red) {
   const int* done = si + SI_DONE;
+  if (op.ff) {
+    // float-float: t = D .* (A^T p) in FP64, w = A t + delta p
+    cudaError_t e = split_ff(st, m, op.ld_mpad, w.p, nullptr, op.xh, op.xl, done);
+    if (e != cudaSuccess) return e;
+    e = gemv_rows_ff(st, n, m, static_cast<const float*>(op.AT), op.ldat, op.xh, op.xl, op.D64, 0.0, nullptr,
+                     op.t64, done, nullptr, op.part, op.part_cap);
+    if (e != cudaSuccess) return e;
+    e = split_ff(st, n, op.ld_npad, op.t64, nullptr, op.xh, op.xl, done);
+    if (e != cudaSuccess) return e;
+    e = gemv_rows_ff(st, m, n, static_cast<const float*>(op.A), op.lda, op.xh, op.xl, nullptr, 1.0, w.p, w.w, done,
+                     sd + SD_DELTA, op.part, op.part_cap);
+    if (e != cudaSuccess) return e;
+    return pcg_tail(st, m, ell, U, ld, w, sd, si, red);
+  }
   // pf = FP32(p);  tf = Df .* (A^T pf);  w = A tf + delta p
   cudaError_t e = to_f32(st, m, op.ld_mpad, w.p, nullptr, op.xf, done);
   if (e != cudaSuccess) return e;
-  e = gemv_rows_lp(st, n, m, op.bf16, op.AT, op.ldat, op.xf, op.Df, 0.0, nullptr, op.tf, 0, done);
+  e = gemv_rows_lp(st, n, m, op.bf16, op.AT, op.ldat, op.xf, op.Df, 0.0, nullptr, op.tf, 0, done, nullptr, op.part,
+                   op.part_cap);
   if (e != cudaSuccess) return e;
-  e = gemv_rows_lp(st, m, n, op.bf16, op.A, op.lda, op.tf, nullptr, 1.0, w.p, w.w, 1, done, sd + SD_DELTA);
+  e = gemv_rows_lp(st, m, n, op.bf16, op.A, op.lda, op.tf, nullptr, 1.0, w.p, w.w, 1, done, sd + SD_DELTA, op.part,
+                   op.part_cap);
   if (e != cudaSuccess) return e;
   return pcg_tail(st, m, ell, U, ld, w, sd, si, red);
 }

@@ -71,6 +71,7 @@ struct nys_solver {
   int gk_m = 0, gk_n = 0, gk_ell = 0, gk_ld = 0;
   unsigned g_kernels_per_iter = 0;
   bool use_graphs = true;
+  bool use_persistent = true;   // one cooperative launch per PCG solve for small problems
   int gk_op = -1;            // graph key: operator kind
   double* pcg_x = nullptr;   // PCG solution buffer (copied out after each solve)
   // precision form (precision_mode 1): A is FP32 (the problem definition);
@@ -84,6 +85,10 @@ struct nys_solver {
   size_t upart_cap = 0;
   long long ld_b = 0, ld_bt = 0, ld_ft = 0, ld_om = 0, ld_tb = 0, ld_ff = 0;
   double *nd_m = nullptr, *u_n = nullptr, *rr = nullptr, *dyacc = nullptr, *ecorr = nullptr;
+  double* lp_part = nullptr;   // column-split partial sums of the row GEMVs
+  size_t lp_part_cap = 0;
+  bool lp_bf16_stage = true;   // BF16 corrections still contracting in this solve
+  int trace = 0;               // NYS_TRACE=1: one line per IPM iteration on stderr
   // batching form: worker solvers (created on first use), one per in-flight QP
   int max_batch = 0;
   std::vector<nys_solver*> workers;
@@ -216,6 +221,8 @@ size_t carve_lp(nys_solver* h, char* base) {
   h->rr = c.take<double>(M);
   h->dyacc = c.take<double>(M);
   h->ecorr = c.take<double>(M);
+  h->lp_part_cap = 16 * std::max(M, N);
+  h->lp_part = c.take<double>(h->lp_part_cap);
   return c.off;
 }
 
@@ -277,7 +284,7 @@ cudaError_t issue_pcg_iteration(nys_solver* h, cudaStream_t st, int m, int n, co
 // issues iterations from the host).
 bool ensure_pcg_graph(nys_solver* h, int m, int n, const OpSpec& op, int ell, const double* U, int ld) {
   if (!h->use_graphs) return false;
-  const double* D = op.kind == 0 ? op.D : reinterpret_cast<const double*>(op.lp.Df);
+  const double* D = op.kind == 0 ? op.D : (op.kind == 3 ? op.lp.D64 : reinterpret_cast<const double*>(op.lp.Df));
   const long long lda = op.kind == 0 ? op.lda : op.lp.lda;
   if (h->pcg_exec && h->gk_op == op.kind && h->gk_A == op.key() && h->gk_lda == lda && h->gk_m == m &&
       h->gk_n == n && h->gk_ell == ell && h->gk_D == D && h->gk_U == U && h->gk_ld == ld)
@@ -335,6 +342,21 @@ int run_pcg(nys_solver* h, int m, int n, const OpSpec& op, double delta, int ell
             int* iters) {
   PcgWork w = h->pw;
   w.x = h->pcg_x;
+  if (op.kind == 0 && h->use_persistent && pcg_persistent_fits(m, n, ell)) {
+    // small problem: the whole solve in one cooperative launch
+    CK(pcg_persistent_f64(h->st, m, n, op.A, op.lda, op.D, delta, ell, U, ld, lamh, xi, eta, max_iter, forced,
+                          w, h->red.part, RedBuf::kPartCap, h->cw.bar, h->sd, h->si, h->num_sms));
+    CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    int rc = sync_scalars(h, 0);
+    if (rc != NYS_OK) return rc;
+    *iters = h->h_si[SI_ITERS];
+    if (forced < 0 && *iters >= max_iter) {
+      CK(cudaMemcpyAsync(h->h_red, h->sd, sizeof(double) * SD_COUNT, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      if (!(h->h_red[SD_RR] <= h->h_red[SD_ETA2] * h->h_red[SD_BNORM2])) return NYS_WARN_PCG_MAXITER;
+    }
+    return NYS_OK;
+  }
   CK(pcg_setup_f64(h->st, m, ell, U, ld, lamh, delta, xi, eta, max_iter, forced, w, h->sd, h->si, h->red));
   const int limit = forced >= 0 ? forced : max_iter;
   if (ensure_pcg_graph(h, m, n, op, ell, U, ld)) {
@@ -408,7 +430,8 @@ int op_Ax(nys_solver* h, const Prob& P, const double* x, double beta, const doub
     CK(gemv_n_f64(h->st, P.m, P.n, P.A64, P.lda, x, beta, v, out));
   } else {
     CK(split_ff(h->st, P.n, (int)align_up(P.n, 8), x, nullptr, h->fh, h->fl));
-    CK(gemv_rows_ff(h->st, P.m, P.n, P.Af, P.lda, h->fh, h->fl, nullptr, beta, v, out));
+    CK(gemv_rows_ff(h->st, P.m, P.n, P.Af, P.lda, h->fh, h->fl, nullptr, beta, v, out, nullptr, nullptr,
+                    h->lp_part, h->lp_part_cap));
   }
   return NYS_OK;
 }
@@ -419,7 +442,8 @@ int op_Aty(nys_solver* h, const Prob& P, const double* y, const double* scale, d
     CK(gemv_t_f64(h->st, P.m, P.n, P.A64, P.lda, y, scale, out, h->split_buf, h->split_cap));
   } else {
     CK(split_ff(h->st, P.m, (int)align_up(P.m, 8), y, nullptr, h->fh, h->fl));
-    CK(gemv_rows_ff(h->st, P.n, P.m, h->AfT, h->ld_ft, h->fh, h->fl, scale, 0.0, nullptr, out));
+    CK(gemv_rows_ff(h->st, P.n, P.m, h->AfT, h->ld_ft, h->fh, h->fl, scale, 0.0, nullptr, out, nullptr, nullptr,
+                    h->lp_part, h->lp_part_cap));
   }
   return NYS_OK;
 }
@@ -450,10 +474,35 @@ int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D) {
 }
 
 // Precision-form Newton direction: Algorithm 4 with the normal equations
-// solved by iterative refinement.  xi, the refinement residual and the back
-// substitution use the FP32 problem matrix with float-float accumulation; the
-// corrections come from Nystrom PCG on the BF16 operator (FP32 once the
-// refinement stops contracting).
+// solved in two stages.  xi, the refinement residual and the back
+// substitution use the FP32 problem matrix with float-float accumulation.
+// Stage 1 (iterative refinement): corrections from Nystrom PCG on the BF16
+// operator, while each one at least halves the residual (mixed-precision
+// refinement contracts only while kappa * u_bf16 < 1).  Stage 2: one PCG solve
+// of the remaining residual on the float-float FP32 operator, which is the
+// problem's operator to ~1e-13, to the outer tolerance.
+LpOperator make_lp_op(nys_solver* h, const Prob& P, int kind, const double* D) {
+  LpOperator op{};
+  op.ff = kind == 3;
+  op.D64 = D;
+  op.t64 = h->u_n;
+  op.xh = h->fh;
+  op.xl = h->fl;
+  op.ld_npad = (int)align_up(P.n, 8);
+  op.bf16 = kind == 1;
+  op.A = kind == 1 ? (const void*)h->Ab : (const void*)P.Af;
+  op.lda = kind == 1 ? h->ld_b : P.lda;
+  op.AT = kind == 1 ? (const void*)h->AbT : (const void*)h->AfT;
+  op.ldat = kind == 1 ? h->ld_bt : h->ld_ft;
+  op.Df = h->Df;
+  op.xf = h->xf;
+  op.tf = h->tf;
+  op.ld_mpad = (int)h->ld_bt;
+  op.part = h->lp_part;
+  op.part_cap = h->lp_part_cap;
+  return op;
+}
+
 int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, const double* D, double delta,
               const double* r_d, const double* r_p, const double* r_xz, int ell, double eta, int max_iter,
               double* dx, double* dy, double* dz, int* iters, int* refine) {
@@ -468,23 +517,18 @@ int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, co
   CK(cudaMemsetAsync(h->dyacc, 0, sizeof(double) * m, h->st));
   CK(cudaMemcpyAsync(h->rr, h->xi, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
   CK(to_f32(h->st, n, (int)align_up(n, 8), D, nullptr, h->Df));
-  double rn = xin, rn_prev = xin;
+  double rn = xin;
   int total = 0, steps = 0, warn = NYS_OK;
-  bool fp32_inner = false;
-  const int max_steps = 12;
-  while (xin > 0.0 && rn > eta * xin && steps < max_steps) {
+  bool bf16_stage = h->lp_bf16_stage;
+  const int max_bf16_steps = 6;
+  while (xin > 0.0 && rn > eta * xin) {
+    const bool final_stage = !bf16_stage || steps >= max_bf16_steps;
     OpSpec op{};
-    op.kind = fp32_inner ? 2 : 1;
-    op.lp.bf16 = fp32_inner ? 0 : 1;
-    op.lp.A = fp32_inner ? (const void*)P.Af : (const void*)h->Ab;
-    op.lp.lda = fp32_inner ? P.lda : h->ld_b;
-    op.lp.AT = fp32_inner ? (const void*)h->AfT : (const void*)h->AbT;
-    op.lp.ldat = fp32_inner ? h->ld_ft : h->ld_bt;
-    op.lp.Df = h->Df;
-    op.lp.xf = h->xf;
-    op.lp.tf = h->tf;
-    op.lp.ld_mpad = (int)h->ld_bt;
-    const double eta_in = std::min(0.5, std::max(1e-4, 0.5 * eta * xin / rn));
+    op.kind = final_stage ? 3 : 1;
+    op.lp = make_lp_op(h, P, op.kind, D);
+    // inner tolerance relative to the current residual
+    const double need = eta * xin / rn;
+    const double eta_in = final_stage ? need : std::min(0.5, std::max(1e-3, 0.5 * need));
     int it = 0;
     rc = run_pcg(h, m, n, op, delta, ell, h->U, h->ld, h->lamh, h->rr, h->ecorr, eta_in, max_iter, -1, &it);
     if (rc < 0) return rc;
@@ -492,6 +536,11 @@ int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, co
     total += it;
     ++steps;
     CK(axpby_f64(h->st, m, 1.0, h->ecorr, 1.0, h->dyacc, h->dyacc));
+    if (final_stage) {
+      // the float-float operator is the problem's: its PCG residual is the
+      // outer residual (to ~1e-13), no further correction needed
+      break;
+    }
     // r = xi - (A D A^T + delta I) dy  (FP32 A, float-float sums)
     rc = op_Aty(h, P, h->dyacc, D, h->u_n);
     if (rc != NYS_OK) return rc;
@@ -501,12 +550,14 @@ int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, co
     CK(dot_f64(h->st, m, h->rr, h->rr, h->red_out + 12, h->red));
     rc = sync_scalars_at(h, 12, 1);
     if (rc != NYS_OK) return rc;
-    rn_prev = rn;
+    const double rn_prev = rn;
     rn = std::sqrt(h->h_red[12]);
     if (!std::isfinite(rn)) return fail(h, NYS_ERR_NUMERIC, "non-finite refinement residual");
-    if (rn > 0.5 * rn_prev) fp32_inner = true;   // BF16 corrections no longer contract
+    if (rn > 0.5 * rn_prev) {
+      bf16_stage = false;               // BF16 corrections stopped contracting:
+      h->lp_bf16_stage = false;         // finish this and later systems on the FP32 operator
+    }
   }
-  if (xin > 0.0 && rn > eta * xin && warn == NYS_OK) warn = NYS_WARN_PCG_MAXITER;
   CK(cudaMemcpyAsync(dy, h->dyacc, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
   rc = op_Aty(h, P, dy, nullptr, h->g_n);
   if (rc != NYS_OK) return rc;
@@ -593,6 +644,8 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
     return NYS_ERR_CUDA;
   }
   if (const char* env = std::getenv("NYS_NO_GRAPHS")) h->use_graphs = (env[0] == '0');
+  if (const char* env = std::getenv("NYS_PCG_PERSISTENT")) h->use_persistent = (env[0] != '0');
+  if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess) {
     cudaFree(h->arena);
@@ -652,8 +705,10 @@ int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A,
   const int bf = a_dtype == NYS_BF16;
   CK(to_f32(h->st, n, (int)align_up(n, 8), D, nullptr, h->Df));
   CK(to_f32(h->st, m, (int)align_up(m, 8), v, nullptr, h->xf));
-  CK(gemv_rows_lp(h->st, n, m, bf, AT, ldat, h->xf, h->Df, 0.0, nullptr, h->tf, 0));
-  CK(gemv_rows_lp(h->st, m, n, bf, A, lda, h->tf, nullptr, delta, v, out, 1));
+  CK(gemv_rows_lp(h->st, n, m, bf, AT, ldat, h->xf, h->Df, 0.0, nullptr, h->tf, 0, nullptr, nullptr, h->lp_part,
+                  h->lp_part_cap));
+  CK(gemv_rows_lp(h->st, m, n, bf, A, lda, h->tf, nullptr, delta, v, out, 1, nullptr, nullptr, h->lp_part,
+                  h->lp_part_cap));
   return NYS_OK;
 }
 
@@ -904,6 +959,7 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   }
   Prob P{m, n, lp, lp ? nullptr : static_cast<const double*>(Av), lp ? static_cast<const float*>(Av) : nullptr, lda};
   const double* A = P.A64;
+  h->lp_bf16_stage = true;
   if (lp)   // BF16 A and A^T for the inner solves and the sketch, FP32 A^T for residuals
     CK(convert_transpose(h->st, m, n, 0, Av, lda, h->Ab, h->ld_b, h->AbT, h->ld_bt, h->AfT, h->ld_ft));
   const cudaMemcpyKind kin = p->host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -980,12 +1036,19 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
     if (k >= o.max_ipm_iter) { status = NYS_WARN_MAXITER; break; }
 
     // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).
+    auto tk0 = std::chrono::steady_clock::now();
     CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
     rc = op_sketch(h, P, p->k0 + k, ell, h->D);
     if (rc != NYS_OK) { status = rc; break; }
     CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
                         h->cw, h->num_sms));
     const double eta = std::max(1e-10, std::min(1e-2, 0.1 * mu));
+    double t_pre = 0.0;
+    if (h->trace) {
+      cudaStreamSynchronize(h->st);
+      t_pre = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
+    }
+    const int pcg_before = r->pcg_iters_total, ref_before = r->refine_steps;
 
     // Predictor (Algorithm 5, first step).
     int it = 0, ref = 0;
@@ -1029,6 +1092,15 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
     const double ap = 0.995 * std::min(1.0, h->h_red[0]);
     const double ad = 0.995 * std::min(1.0, h->h_red[1]);
     CK(ipm_update_f64(h->st, m, n, ap, ad, h->dxc, h->dyc, h->dzc, h->x, h->y, h->z));
+    if (h->trace) {
+      cudaStreamSynchronize(h->st);
+      const double t_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
+      std::fprintf(stderr,
+                   "[nys] k=%d mu=%.3e rel_p=%.3e rel_d=%.3e rho=%.2e delta=%.2e ap=%.3f ad=%.3f pcg=%d "
+                   "refine=%d sketch+core=%.1fms iter=%.1fms\n",
+                   k, mu, rel_p, rel_d, rho, delta, ap, ad, r->pcg_iters_total - pcg_before,
+                   r->refine_steps - ref_before, 1e3 * t_pre, 1e3 * t_it);
+    }
     mu_prev = mu;
     ++k;
   }

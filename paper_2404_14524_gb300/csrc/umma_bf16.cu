@@ -289,16 +289,30 @@ size_t smem_bytes(int npad) {
   return 1024 + ((sizeof(Smem<kStages>) + 1023) & ~size_t(1023)) + (size_t)kStages * nb * br * kBK * 2;
 }
 
+// Number of K splits, from a simple time model in units of one k-block of
+// MMAs on one SM: waves(S) * (ceil(kb / S) + 16), where a wave is one CTA per
+// SM and 16 k-blocks is the cost of writing and re-reading one 128 x N FP32
+// partial tile at the per-SM share of HBM bandwidth (both scale with N).
+int pick_splits(int M, int N, int K, int num_sms) {
+  (void)N;
+  const int tiles = (M + kBM - 1) / kBM;
+  const int kb = (K + kBK - 1) / kBK;
+  int best = 1;
+  long long best_t = -1;
+  for (int S = 1; S <= 64 && S <= kb; ++S) {
+    const long long units = (long long)tiles * S;
+    const long long waves = (units + num_sms - 1) / num_sms;
+    const long long t = waves * ((kb + S - 1) / S + (S > 1 ? 16 : 0));
+    if (best_t < 0 || t < best_t) { best_t = t; best = S; }
+  }
+  return best;
+}
+
 }  // namespace
 
 size_t umma_part_elems(int M, int N, int K, int num_sms) {
   const int npad = (N + 15) / 16 * 16;
-  const int tiles = (M + kBM - 1) / kBM;
-  const int kb = (K + kBK - 1) / kBK;
-  int S = (2 * num_sms + tiles - 1) / tiles;
-  if (S > kb) S = kb;
-  if (S < 1) S = 1;
-  return (size_t)S * npad * M;
+  return (size_t)pick_splits(M, N, K, num_sms) * npad * M;
 }
 
 cudaError_t umma_gemm_bf16(cudaStream_t st, int M, int N, int K, const void* A, long long lda,
@@ -312,9 +326,7 @@ cudaError_t umma_gemm_bf16(cudaStream_t st, int M, int N, int K, const void* A, 
   if (!make_map(&mb, B, N, K, ldb, br)) return cudaErrorInvalidValue;
   const int tiles = (M + kBM - 1) / kBM;
   const int kb = (K + kBK - 1) / kBK;
-  int S = (2 * num_sms + tiles - 1) / tiles;
-  if (S > kb) S = kb;
-  if (S < 1) S = 1;
+  int S = pick_splits(M, N, K, num_sms);
   while (S > 1 && (size_t)S * npad * M > part_cap) --S;
   const int per = (kb + S - 1) / S;
   S = (kb + per - 1) / per;

@@ -185,11 +185,11 @@ def test_pcg_matches_oracle(nys, m, n, ell, delta):
     want = O.pcg(lambda v: O.normal_matvec(A, D, delta, v), lambda v: O.precond_inv_apply(Fw, delta, v),
                  xi, eta, 1000)
     dy, it, res, rc = nys.nys_pcg(h, T(A), T(D), delta, P(U), T(lam), T(xi), eta, 1000)
-    # Free-running CG decides its exit on a residual that crosses eta within
-    # rounding: the count may differ by one.  Both solutions satisfy the
-    # residual test, so each lies within eta ||xi|| / lambda_min(M) of the
-    # exact solution of the dense system.
-    assert abs(it - want.iters) <= 1 and rc == 0
+    # Free-running CG decides its exit on a residual that crosses eta; on an
+    # ill-conditioned system rounding shifts that crossing by a few percent of
+    # the iterations.  Both solutions satisfy the residual test, so each lies
+    # within eta ||xi|| / lambda_min(M) of the exact solution of the dense system.
+    assert abs(it - want.iters) <= max(2, 0.05 * want.iters) and rc == 0
     M = A @ (D[:, None] * A.T) + delta * np.eye(m)
     exact = np.linalg.solve(M, xi)
     g = dy.cpu().numpy()
@@ -372,3 +372,18 @@ def test_core_breakdown_is_reported_not_trapped(nys):
     # still usable
     out = nys.nys_precond_apply(h, P(np.eye(m)[:, :ell]), T(np.ones(ell)), 1.0, T(np.ones(m)))
     assert torch.isfinite(out).all()
+
+
+def test_persistent_pcg_matches_the_graph_pcg(nys, monkeypatch):
+    """Small systems run the whole PCG in one cooperative launch; it must give
+    the same solution as the multi-kernel (CUDA graph) path."""
+    h1, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, 300, 900, 24, seed=21)
+    xi = np.random.default_rng(4).standard_normal(300)
+    monkeypatch.setenv("NYS_PCG_PERSISTENT", "0")
+    h0 = nys.Handle(300, 900, ell=24)
+    monkeypatch.delenv("NYS_PCG_PERSISTENT")
+    for forced in (5, -1):
+        a, ia, ra, _ = nys.nys_pcg(h1, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
+        b, ib, rb, _ = nys.nys_pcg(h0, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
+        assert abs(ia - ib) <= (0 if forced >= 0 else 1)
+        assert relerr(a, b.cpu().numpy()) <= (1e-11 if forced >= 0 else 1e-7)

@@ -71,3 +71,17 @@ def test_precision_form_meets_kkt_and_tracks_the_fp64_oracle(nys):
           f"{info['refine_steps']} refinement steps; |x - x_oracle| / |x| = {err:.2e}")
     assert err <= 1e-3
     assert info["refine_steps"] >= 2 * info["ipm_iters"]
+
+
+def test_precision_form_with_a_large_sketch(nys):
+    """ell = 128 takes the QR route of the Nystrom core and a 128-column
+    tensor-core sketch; the solve must still meet KKT <= 1e-6 (checked in
+    FP64 on the FP32 problem)."""
+    m, n, ell, tol = 1200, 5000, 128, 1e-6
+    A32, A64, b, c, qp = _qp32(44, m, n)
+    h = nys.Handle(m, n, ell=ell, tol=tol, seed=6, precision_mode=1)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    x, y, z, info = nys.nys_solve(h, T(A32), T(b), T(c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    assert info["status"] in (0, 2), info
+    rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, *(t.cpu().numpy() for t in (x, y, z)))
+    assert rp <= tol and rd <= tol and mu <= tol
