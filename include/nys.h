@@ -186,6 +186,24 @@ int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A,
                          const void* AT, long long ldat, const double* D, double delta, const double* v,
                          double* out);
 
+/* (N + delta I) v = A (D .* (A^T v)) + delta v, as nys_normal_matvec, for
+ * callers that cannot allocate device memory (code running inside a stream
+ * capture or under a memory pool that a cudaMalloc would disturb, hosts that
+ * forbid allocation after start-up, plugins that only receive pointers): it
+ * takes no handle and allocates nothing.  The paper has no counterpart; this
+ * is an interface of this library.
+ * Scratch: one fixed 8 MiB device array inside the library, held by every
+ * GPU that loads it until exit; n <= 1,048,576 (larger n returns
+ * NYS_ERR_NOMEM).  The first call on a device, with that device current,
+ * looks up the array's device address (make it before any stream capture).
+ * All calls share the array: calls that may overlap on the GPU race and must
+ * be serialised by the caller.  A: FP64 row-major m x n (lda >= n); D: n;
+ * v, out: m (out must not alias v); all device pointers; work is issued on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream) and not waited
+ * for.  Errors: NYS_ERR_ARG, NYS_ERR_NOMEM, NYS_ERR_CUDA. */
+int nys_normal_matvec_noalloc(int m, int n, const double* A, long long lda, const double* D, double delta,
+                              const double* v, double* out, void* cuda_stream);
+
 /* Omega_k (m x ell, leading dimension ld): entry (i, j) is the standard normal
  * deviate of Algorithm 1's first step drawn from the SplitMix64 stream of
  * Steele, Lea and Flood (2014) keyed by `seed`, at stream positions 2c and

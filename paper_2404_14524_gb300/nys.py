@@ -86,6 +86,7 @@ _SIGS = {
     "nys_scaling": (_I, [_P, _I, _P, _P, _P, _D, _P]),
     "nys_normal_matvec": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _P, _P]),
     "nys_normal_matvec_lp": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _D, _P, _P]),
+    "nys_normal_matvec_noalloc": (_I, [_I, _I, _P, _LL, _P, _D, _P, _P, _P]),
     "nys_gaussian": (_I, [_P, ctypes.c_ulonglong, _I, _I, _I, _P, _I]),
     "nys_sketch": (_I, [_P, _I, _I, _I, _P, _LL, _P, _I, _P, _P, _I]),
     "nys_nystrom": (_I, [_P, _I, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_D)]),
@@ -232,6 +233,16 @@ def nys_normal_matvec_lp(h: Handle, A, AT, D, delta: float, v, out=None):
     h.check(lib().nys_normal_matvec_lp(h.h, m, n, dt, _ptr(A), A.stride(0), _ptr(AT), AT.stride(0),
                                        _ptr(_f64(D, "D")), float(delta), _ptr(_f64(v, "v")), _ptr(_f64(out, "out"))))
     return out
+
+
+def nys_normal_matvec_noalloc(A, D, delta: float, v, out, stream=None) -> int:
+    """(N + delta I) v with no handle and no allocation (fixed library scratch;
+    see include/nys.h).  `out` must be preallocated; returns the status code."""
+    m, n = A.shape
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(lib().nys_normal_matvec_noalloc(m, n, _ptr(_f64(A, "A")), A.stride(0), _ptr(_f64(D, "D")),
+                                               float(delta), _ptr(_f64(v, "v")), _ptr(_f64(out, "out")),
+                                               ctypes.c_void_p(st.cuda_stream)))
 
 
 def nys_gaussian(h: Handle, seed: int, k: int, m: int, ell: int, out=None):
