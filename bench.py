@@ -502,7 +502,7 @@ def profile_kernel(args):
         ell = args.ell
         A = (torch.randn(m, n, generator=g, device=dev) / 100).to(torch.bfloat16)
         B = (torch.randn(ell, n, generator=g, device=dev) / 100).to(torch.bfloat16)
-        h = nys.Handle(m, 64, ell=ell, precision_mode=1)
+        h = nys.Handle(m, n, ell=ell, precision_mode=1)   # workspace sized for K=n: split-K is not capped
         run = lambda: nys.nys_gemm_bf16(h, A, B)
         work = {"bytes": 2.0 * m * n, "flops": 2.0 * m * n * ell}
     run()
