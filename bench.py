@@ -261,6 +261,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gemv", action="store_true",
+                    help="skip the operator GEMV measurement at the large workload shapes")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision workloads: also time one FP64-form solve of the same QP")
     ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm"],
@@ -336,12 +338,13 @@ def main():
         torch.cuda.synchronize(dev)
         l0 = nys.nys_kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        runs = []
+        runs, timed = [], []
         t_wall = time.perf_counter()
         with ClockSampler(local) as clk:
             e0.record(stream)
             for _ in range(args.steps):
                 runs = step()
+                timed.extend(runs)
             e1.record(stream)
             torch.cuda.synchronize(dev)
         t_wall = time.perf_counter() - t_wall
@@ -360,13 +363,32 @@ def main():
         per_step = len(dev_probs)
         value = args.steps * per_step * world / (ms / 1e3)
 
-        # ---- roofline of the dominant kernel (the normal-equations operator)
+        # ---- roofline of the dominant kernel
         A0 = dev_probs[0][0]
         m0, n0 = A0.shape
         hbm_peak, bf16_peak, peak_src = measured_peaks()
-        if form == "bf16":
+        routes = sorted({nys.ROUTE_NAMES[nys.nys_pcg_route(h, pr[0].shape[0], pr[0].shape[1], pr[7])]
+                         for pr in dev_probs}) if form != "bf16" else ["graph"]
+        pcg_iters = sum(i["pcg_iters_total"] for i in timed)
+        pcg_s = sum(i["pcg_seconds"] for i in timed)
+        pcg = {"routes": routes, "iters": pcg_iters, "device_s": pcg_s,
+               "us_per_iter": 1e6 * pcg_s / max(pcg_iters, 1)}
+        if form != "bf16" and "graph" not in routes and pcg_s > 0:
+            # one launch per PCG solve (thread-block cluster or cooperative grid):
+            # that kernel dominates; its algorithmic FP64 work per iteration is
+            # the operator (4 m n), the preconditioner (4 m ell) and the CG
+            # vector updates and dots (12 m)
+            fl = sum(pcg_flops_per_iter(pr[0].shape[0], pr[0].shape[1], pr[7]) * i["pcg_iters_total"]
+                     for pr, i in zip(dev_probs * args.steps, timed))
+            peak = fp64_alu_peak_tflops()
+            roofline = {"bound": "alu", "achieved": fl / pcg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": fl / pcg_s / 1e12 / peak, "traffic": None,
+                        "kernel": "whole-PCG kernel (" + ", ".join(routes) + "), one launch per Newton solve",
+                        "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
+                        "launch_avg_ms": 1e3 * pcg_s / max(1, 2 * sum(i["ipm_iters"] for i in timed)),
+                        "algorithmic_flops": fl}
+        elif form == "bf16":
             # BF16 operator: A^T pass over the BF16 transpose + A pass, FP32 accumulation
-            flops = 4.0 * m0 * n0
             bytes_alg = 2.0 * m0 * n0 * 2 + 4.0 * (3 * m0 + 2 * n0)
             op_s = time_lp_operator(nys, h, A0, stream)
             roofline = {"bound": "hbm", "achieved": bytes_alg / op_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -375,31 +397,7 @@ def main():
                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})", "op_ms": op_s * 1e3,
                         "algorithmic_bytes": bytes_alg}
         else:
-            flops = 4.0 * m0 * n0
-            bytes_alg = 2.0 * m0 * n0 * 8 + 8.0 * (3 * m0 + 2 * n0)
-            D = torch.rand(n0, dtype=torch.float64, device=dev) + 0.5
-            v = torch.randn(m0, dtype=torch.float64, device=dev)
-            out = torch.empty_like(v)
-            for _ in range(3):
-                nys.nys_normal_matvec(h, A0, D, 1e-3, v, out)
-            reps = 50
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for _ in range(reps):
-                nys.nys_normal_matvec(h, A0, D, 1e-3, v, out)
-            f1.record(stream)
-            torch.cuda.synchronize(dev)
-            op_s = f0.elapsed_time(f1) / reps / 1e3
-            peak = fp64_alu_peak_tflops()
-            tr = traffic_record("gemv_f64.cu", "fp64_operator")
-            roofline = {"bound": "alu", "achieved": flops / op_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "frac": flops / op_s / 1e12 / peak,
-                        "traffic": (tr["bytes_per_element"] * m0 * n0) if tr else None,
-                        "kernel": "FP64 normal-equations operator (k_atv_partial + k_atv_reduce + k_av)",
-                        "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
-                        "hbm_gbs": bytes_alg / op_s / 1e9, "op_ms": op_s * 1e3,
-                        "algorithmic_flops": flops, "algorithmic_bytes": bytes_alg}
-
+            roofline = fp64_operator_roofline(nys, h, A0, stream)
         # ---- e2e: the same solves through the C ABI from pinned host buffers
         e2e = None
         if form in ("fp64", "bf16"):
@@ -423,6 +421,9 @@ def main():
         else:
             e2e = {"value": None, "unit": "QP solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                    "note": "batch/diff workloads take device tensors only"}
+
+        # the GEMV pairs at the large workload shapes (the metric's GEMV GB/s)
+        gemv = operator_rooflines(nys, dev, stream) if (rank == 0 and not args.no_gemv) else None
 
         fp64_cmp = None
         if form == "bf16" and args.compare_fp64:
@@ -468,6 +469,9 @@ def main():
         }
         if fp64_cmp is not None:
             line["fp64_form_same_qp"] = fp64_cmp
+        line["pcg"] = pcg
+        if gemv is not None:
+            line["gemv"] = gemv
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
@@ -516,6 +520,84 @@ def profile_kernel(args):
     sec = e0.elapsed_time(e1) / reps / 1e3
     print(json.dumps({"kernel": args.profile_kernel, "m": m, "n": n, "reps": reps, "ms": sec * 1e3,
                       "GB/s": work["bytes"] / sec / 1e9, "TFLOP/s": work["flops"] / sec / 1e12}), flush=True)
+
+
+def pcg_flops_per_iter(m, n, ell):
+    """Algorithmic FP64 flops of one PCG iteration: A^T p and A t (4 m n),
+    U^T r and U s (4 m ell), and the CG dots and updates (12 m)."""
+    return 4.0 * m * n + 4.0 * m * ell + 12.0 * m
+
+
+def fp64_operator_roofline(nys, h, A0, stream, reps=50):
+    """FP64 operator (A^T pass, reduction, A pass) timed with CUDA events on
+    `stream`: DFMA-bound, reported against the nominal FP64 rate."""
+    import torch
+    dev = A0.device
+    m0, n0 = A0.shape
+    flops = 4.0 * m0 * n0
+    bytes_alg = 2.0 * m0 * n0 * 8 + 8.0 * (3 * m0 + 2 * n0)
+    D = torch.rand(n0, dtype=torch.float64, device=dev) + 0.5
+    v = torch.randn(m0, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    for _ in range(3):
+        nys.nys_normal_matvec(h, A0, D, 1e-3, v, out)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(reps):
+        nys.nys_normal_matvec(h, A0, D, 1e-3, v, out)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    op_s = f0.elapsed_time(f1) / reps / 1e3
+    peak = fp64_alu_peak_tflops()
+    tr = traffic_record("gemv_f64.cu", "fp64_operator")
+    return {"bound": "alu", "achieved": flops / op_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / op_s / 1e12 / peak,
+            "traffic": (tr["bytes_per_element"] * m0 * n0) if tr else None,
+            "kernel": "FP64 normal-equations operator (k_atv_partial + k_atv_reduce + k_av)",
+            "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
+            "hbm_gbs": bytes_alg / op_s / 1e9, "op_ms": op_s * 1e3,
+            "algorithmic_flops": flops, "algorithmic_bytes": bytes_alg}
+
+
+def operator_rooflines(nys, dev, stream):
+    """The two operator GEMV pairs at the large workload shapes (inputs far
+    larger than L2, random entries): FP64 at m=5000, n=20000 and BF16 at
+    m=20000, n=100000."""
+    import torch
+    out = {}
+    g = torch.Generator(device=dev).manual_seed(0)
+    with torch.cuda.stream(stream):
+        A = torch.randn(5000, 20000, generator=g, device=dev, dtype=torch.float64)
+        h = nys.Handle(5000, 20000, ell=8, stream=stream)
+        out["fp64_5000x20000"] = fp64_operator_roofline(nys, h, A, stream, reps=20)
+        h.close()
+        del A
+        m, n = 20000, 100000
+        A = torch.randn(m, n, generator=g, device=dev, dtype=torch.bfloat16)
+        AT = A.T.contiguous()
+        h = nys.Handle(m, n, ell=8, precision_mode=1, stream=stream)
+        D = torch.rand(n, dtype=torch.float64, device=dev) + 0.5
+        v = torch.randn(m, dtype=torch.float64, device=dev)
+        o = torch.empty_like(v)
+        for _ in range(3):
+            nys.nys_normal_matvec_lp(h, A, AT, D, 1e-3, v, o)
+        reps = 20
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(reps):
+            nys.nys_normal_matvec_lp(h, A, AT, D, 1e-3, v, o)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        op_s = f0.elapsed_time(f1) / reps / 1e3
+        h.close()
+        del A, AT
+    hbm_peak, _, src = measured_peaks()
+    bytes_alg = 2.0 * m * n * 2 + 4.0 * (3 * m + 2 * n)
+    out["bf16_20000x100000"] = {"bound": "hbm", "achieved": bytes_alg / op_s / 1e9, "peak": hbm_peak,
+                                "unit": "GB/s", "frac": bytes_alg / op_s / 1e9 / hbm_peak, "op_ms": op_s * 1e3,
+                                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
+    torch.cuda.empty_cache()
+    return out
 
 
 def time_lp_operator(nys, h, A32, stream):

@@ -104,6 +104,8 @@ typedef struct {
     double rel_gap;               /* |pobj - dobj| / (1 + |pobj|)                      */
     double rho, delta;            /* final PMM regularisation                          */
     double seconds;               /* wall time inside nys_solve                        */
+    double pcg_seconds;           /* device time of the PCG solves (CUDA events on the */
+                                  /*   handle's stream around each solve)              */
     int* pcg_log;                 /* optional host array: PCG iterations per Newton   */
     int pcg_log_cap;              /*   solve, in order (capacity in entries)           */
     int pcg_log_len;              /* entries written                                   */
@@ -243,6 +245,20 @@ int nys_pcg(nys_handle h, int m, int n, int a_dtype, const void* A, long long ld
             const double* D, double delta, int ell, const double* U, int ld, const double* lam,
             const double* xi, double* dy, double eta, int max_iter, int forced_iters,
             int* iters, double* res_norm);
+
+/* Which implementation nys_pcg / nys_solve use for an FP64 system of this
+ * size (the same arithmetic in each; they differ only in summation order):
+ *   NYS_ROUTE_CLUSTER_SMEM  one thread-block cluster, A's column bands in
+ *                           shared memory (small A);
+ *   NYS_ROUTE_CLUSTER_L2    one thread-block cluster, A read from L2;
+ *   NYS_ROUTE_COOPERATIVE   one cooperative grid-wide launch;
+ *   NYS_ROUTE_GRAPH         one CUDA-graph launch of per-step kernels.
+ * The choice depends only on (m, n, ell), the device and the environment
+ * variable NYS_PCG_PATH (cluster | cooperative | graph) read at nys_create.
+ * Returns the route, or NYS_ERR_ARG for a null handle or sizes <= 0.
+ * The paper has no counterpart: its PCG runs on a CPU. */
+enum { NYS_ROUTE_CLUSTER_SMEM = 0, NYS_ROUTE_CLUSTER_L2 = 1, NYS_ROUTE_COOPERATIVE = 2, NYS_ROUTE_GRAPH = 3 };
+int nys_pcg_route(nys_handle h, int m, int n, int ell);
 
 /* Newton direction through the normal equations (Algorithm 4 with I = all):
  * xi_au = -X^{-1} r_xz; xi = r_p + A D (r_d + xi_au); (N + delta I) dy = xi by

@@ -129,27 +129,30 @@ __device__ bool grid_min(double v, double* partials, unsigned int* counter, doub
 }
 
 // Bounded grid barrier for cooperative launches (all blocks co-resident).
-// `bar` points to two words: [0] arrival count, [1] generation.  A block that
-// waits longer than the spin limit records kErrTimeout in *err and returns
-// false; so does every block once *err is non-zero.
+// `bar` is one word that must be zero when the launch starts; each barrier
+// leaves its low 31 bits at zero again.  Block 0 adds 2^31 - (blocks - 1),
+// every other block adds 1, so the top bit flips exactly when the last block
+// arrives, whatever the arrival order; a waiting block watches for that flip.
+// One atomic per block and one polled word: no reset step, no second round
+// trip.  A block that waits longer than the spin limit records kErrTimeout in
+// *err and returns false; so does every block once *err is non-zero.
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = bar + 1;
+    const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
     volatile int* verr = err;
-    const unsigned int g = *gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*gen == g && *verr == 0) {
-        if (++spins > (1ull << 24)) { set_error(err, kErrTimeout); break; }
-        __nanosleep(64);
+    __threadfence();                       // this block's writes before its arrival
+    const unsigned int old = atomicAdd(bar, inc);
+    unsigned long long spins = 0;
+    while (true) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+      if ((cur ^ old) & 0x80000000u) break;
+      if ((++spins & 31u) == 0) {
+        if (*verr != 0) break;
+        if (spins > (1ull << 24)) { set_error(err, kErrTimeout); break; }
+        __nanosleep(32);
       }
     }
     __threadfence();

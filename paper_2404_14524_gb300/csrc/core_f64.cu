@@ -3,26 +3,26 @@
 //   C = chol(G) (upper, G = C^T C);  B = Y_nu C^{-1};  thin SVD of B;
 //   lam = max(0, Sigma^2 - nu) in descending order, U = left singular vectors.
 //
-// The thin SVD is a one-sided (Hestenes) Jacobi iteration, run as one
-// cooperative launch: each round rotates ell/2 disjoint column pairs in
-// parallel (one CTA per pair, round-robin ordering), with a bounded grid
-// barrier between rounds.  One-sided Jacobi orthogonalises columns directly,
+// The thin SVD is a one-sided (Hestenes) Jacobi iteration: each round
+// rotates ell/2 disjoint column pairs in parallel (round-robin ordering), with
+// a barrier between rounds.  One-sided Jacobi orthogonalises columns directly,
 // so small singular values keep their relative accuracy (no Gram matrix, no
 // squared condition number).  After convergence the column norms are the
 // singular values and the normalised columns the left singular vectors.
-// For ell <= 96 it runs on B itself; for larger ell on the triangular factor
-// R of B = Q R (shifted three-pass Cholesky QR), and B V = Q (R V).
+// When B is nearly square (m <= 2 ell) and fits one CTA's shared memory it
+// runs on B itself; otherwise on the triangular factor R of B = Q R (shifted
+// three-pass Cholesky QR), and B V = Q (R V).  A sweep over B costs about
+// 3.5 m ell^2 DFMAs, over R 3.5 ell^3, and the FP64 rate of one SM is the
+// bound of the rotations, so the QR route wins as soon as m is a few times
+// ell.  Matrices of up to 25600 entries are rotated by a single CTA in shared
+// memory (__syncthreads between rounds); larger ones by the cooperative
+// kernel with grid barriers.
 #include "common.cuh"
 #include "internal.h"
 
 namespace nys {
 
 namespace {
-
-// Above this sketch size the thin SVD goes through a QR of B first: one-sided
-// Jacobi directly on B costs ~3.5 m ell^2 DFMAs per sweep (8-10 sweeps),
-// the QR route ~4 m ell^2 DFMAs in total plus sweeps on an ell x ell matrix.
-constexpr int kJacobiDirectMaxEll = 96;
 
 __global__ void __launch_bounds__(kNT) k_frob(int m, int ell, const double* __restrict__ Y, int ld,
                                               double* sd, int* err, double* part, unsigned* cnt) {
@@ -105,6 +105,58 @@ __global__ void __launch_bounds__(kNT) k_chol(int ell, double* G, int* err) {
   }
 }
 
+// The same factorisation with G in shared memory (ell <= 160), right-looking:
+// for each j, the pivot's root and reciprocal root (independent, so their
+// latencies overlap), row j of C scaled by the reciprocal, then a rank-one
+// update of the trailing upper triangle.
+constexpr int kCholSmemMax = 160;
+
+__global__ void __launch_bounds__(kNT) k_chol_smem(int ell, double* G, int* err) {
+  extern __shared__ double S[];          // ell x ell, column-major: (a, c) at c * ell + a
+  __shared__ double piv[2];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const int n2 = ell * ell;
+  for (int idx = tid; idx < n2; idx += kNT) {
+    const int a = idx % ell, c = idx / ell;
+    S[idx] = a == c ? G[idx] : 0.5 * (G[(size_t)c * ell + a] + G[(size_t)a * ell + c]);
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < ell; ++j) {
+    if (tid == 0) {
+      const double d = S[j * ell + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+      } else {
+        piv[0] = sqrt(d);
+        piv[1] = rsqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double inv = piv[1];
+    for (int c = j + 1 + tid; c < ell; c += kNT) S[c * ell + j] *= inv;   // C(j, c)
+    __syncthreads();
+    if (tid == 0) S[j * ell + j] = piv[0];
+    // S(a, c) -= C(j, a) C(j, c) for j < a <= c
+    const int w = ell - j - 1;
+    for (int idx = tid; idx < w * w; idx += kNT) {
+      const int a = j + 1 + idx % w, c = j + 1 + idx / w;
+      if (a <= c) S[c * ell + a] = fma(-S[a * ell + j], S[c * ell + j], S[c * ell + a]);
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) set_error(err, kErrCoreBreakdown);
+    return;
+  }
+  for (int idx = tid; idx < n2; idx += kNT) {
+    const int a = idx % ell, c = idx / ell;
+    G[idx] = a <= c ? S[idx] : 0.0;
+  }
+}
+
 // B = Y_nu C^{-1} in place, one thread per row: b_j = (y_j - sum_{k<j} b_k C_kj) / C_jj.
 __global__ void __launch_bounds__(kNT) k_trsm_rows(int m, int ell, double* __restrict__ B, int ld,
                                                    const double* __restrict__ C, const int* err) {
@@ -119,7 +171,75 @@ __global__ void __launch_bounds__(kNT) k_trsm_rows(int m, int ell, double* __res
   }
 }
 
+// The same substitution with the thread's row staged in shared memory
+// (re-read from there instead of from global memory), the reciprocals of the
+// diagonal computed once, and four partial sums per step; 128 rows per CTA,
+// ell <= 200.
+constexpr int kTrsmRows = 128;
+constexpr int kTrsmSmemMax = 200;
+
+__global__ void __launch_bounds__(kTrsmRows) k_trsm_smem(int m, int ell, double* __restrict__ B, int ld,
+                                                         const double* __restrict__ C, const int* err) {
+  extern __shared__ double sm[];         // rows: [ell][kTrsmRows], then 1 / C_jj
+  double* rows = sm;
+  double* invd = sm + (size_t)ell * kTrsmRows;
+  if (*err) return;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < ell; j += kTrsmRows) invd[j] = 1.0 / C[(size_t)j * ell + j];
+  const int i = blockIdx.x * kTrsmRows + tid;
+  const bool act = i < m;
+  if (act)
+    for (int j = 0; j < ell; ++j) rows[j * kTrsmRows + tid] = B[(size_t)j * ld + i];
+  __syncthreads();
+  if (!act) return;
+  for (int j = 0; j < ell; ++j) {
+    const double* cj = C + (size_t)j * ell;
+    double s0 = rows[j * kTrsmRows + tid], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 4 <= j; k += 4) {
+      s0 = fma(-rows[(k + 0) * kTrsmRows + tid], __ldg(cj + k + 0), s0);
+      s1 = fma(-rows[(k + 1) * kTrsmRows + tid], __ldg(cj + k + 1), s1);
+      s2 = fma(-rows[(k + 2) * kTrsmRows + tid], __ldg(cj + k + 2), s2);
+      s3 = fma(-rows[(k + 3) * kTrsmRows + tid], __ldg(cj + k + 3), s3);
+    }
+    for (; k < j; ++k) s0 = fma(-rows[k * kTrsmRows + tid], __ldg(cj + k), s0);
+    rows[j * kTrsmRows + tid] = ((s0 + s1) + (s2 + s3)) * invd[j];
+  }
+  for (int j = 0; j < ell; ++j) B[(size_t)j * ld + i] = rows[j * kTrsmRows + tid];
+}
+
 // One-sided Jacobi on the columns of B (m x ell).  Cooperative launch.
+// Whether columns with squared norms al, be and inner product ga still need
+// a rotation: |ga| > tol sqrt(al be), tested on squares when al be is in range
+// (FP64 square roots and divisions have long latencies on this GPU).
+__device__ __forceinline__ bool jacobi_needs_rotation(double al, double be, double ga, double tol) {
+  if (!(al > 0.0) || !(be > 0.0)) return false;
+  const double ab = al * be;
+  if (ab > 0x1.0p-900 && ab < 0x1.0p+900) return ga * ga > (tol * tol) * ab;
+  return fabs(ga) > tol * sqrt(al) * sqrt(be);
+}
+
+// Rotation (c, s) that zeroes the inner product (Rutishauser's formulas):
+// zeta = (be - al) / (2 ga), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1 / sqrt(1 + t^2), s = c t.  For |zeta| > 2^13 the first-order angle
+// t = ga / (be - al) is used with c = 1 - t^2 / 2, which is orthogonal to
+// double precision (c^2 (1 + t^2) = 1 - O(t^4), t^4 < 2^-56); the small angle
+// error only leaves a residual inner product of relative size 1/(4 zeta^2)
+// for the next sweep.  One division instead of three divisions and two roots.
+__device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double& c, double& s) {
+  const double d = be - al;
+  if (fabs(d) > 16384.0 * fabs(ga)) {
+    const double t = ga / d;
+    c = fma(-0.5 * t, t, 1.0);
+    s = c * t;
+  } else {
+    const double zeta = d / (2.0 * ga);
+    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+    c = 1.0 / sqrt(fma(t, t, 1.0));
+    s = c * t;
+  }
+}
+
 __global__ void __launch_bounds__(kNT) k_jacobi(int m, int ell, double* B, int ld, double tol,
                                                 int* sweep_flags, int max_sweeps, unsigned* bar,
                                                 int* err, int* sweeps_out) {
@@ -150,14 +270,9 @@ __global__ void __launch_bounds__(kNT) k_jacobi(int m, int ell, double* B, int l
         }
         block_sum<kNT, 3>(v, sh);
         const double al = v[0], be = v[1], ga = v[2];
-        if (al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          // Rotation that zeroes the inner product (Rutishauser's formulas).
-          const double zeta = (be - al) / (2.0 * ga);
-          double t;
-          if (fabs(zeta) > 1e150) t = 0.5 / zeta;
-          else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double c = 1.0 / sqrt(fma(t, t, 1.0));
-          const double s = c * t;
+        if (jacobi_needs_rotation(al, be, ga, tol)) {
+          double c, s;
+          jacobi_rotation(al, be, ga, c, s);
           for (int i = tid; i < m; i += kNT) {
             const double x = __ldcg(bp + i), y = __ldcg(bq + i);
             __stcg(bp + i, c * x - s * y);
@@ -177,6 +292,83 @@ __global__ void __launch_bounds__(kNT) k_jacobi(int m, int ell, double* B, int l
     }
   }
   if (blockIdx.x == 0 && tid == 0) *sweeps_out = max_sweeps + 1;   // not converged
+}
+
+// The same Jacobi iteration on one CTA with the matrix in shared memory, for
+// matrices of up to kJacobiSmemElems entries: a warp per column pair, a
+// __syncthreads between rounds instead of a grid barrier.  Pair order,
+// rotation formulas and the stopping rule are those of k_jacobi.
+constexpr int kJT = 1024;
+constexpr int kJW = kJT / 32;
+constexpr int kJacobiSmemElems = 25600;   // 200 KB of doubles
+
+__global__ void __launch_bounds__(kJT) k_jacobi_smem(int m, int ell, double* B, int ld, double tol,
+                                                     int max_sweeps, int* err, int* sweeps_out) {
+  extern __shared__ double M[];          // m x ell, column-major, ld = m
+  __shared__ int rotated;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (*err) return;
+  for (long long e = tid; e < (long long)m * ell; e += kJT) {
+    const int i = (int)(e % m), c = (int)(e / m);
+    M[e] = B[(size_t)c * ld + i];
+  }
+  const int lp = ell + (ell & 1);
+  const int npairs = lp / 2;
+  const int rounds = lp - 1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < rounds; ++r) {
+      for (int pi = wid; pi < npairs; pi += kJW) {
+        int p, q;
+        if (pi == 0) { p = r; q = lp - 1; }
+        else { p = (r + pi) % (lp - 1); q = (r - pi + (lp - 1)) % (lp - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= ell) continue;
+        double* bp = M + (size_t)p * m;
+        double* bq = M + (size_t)q * m;
+        double al = 0.0, be = 0.0, ga = 0.0, al2 = 0.0, be2 = 0.0, ga2 = 0.0;
+        int i = lane;
+        for (; i + 32 < m; i += 64) {
+          const double x = bp[i], y = bq[i], x2 = bp[i + 32], y2 = bq[i + 32];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+          al2 = fma(x2, x2, al2);
+          be2 = fma(y2, y2, be2);
+          ga2 = fma(x2, y2, ga2);
+        }
+        if (i < m) {
+          const double x = bp[i], y = bq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al + al2);
+        be = warp_sum(be + be2);
+        ga = warp_sum(ga + ga2);
+        if (jacobi_needs_rotation(al, be, ga, tol)) {
+          double c, sn;
+          jacobi_rotation(al, be, ga, c, sn);
+          for (int i = lane; i < m; i += 32) {
+            const double x = bp[i], y = bq[i];
+            bp[i] = c * x - sn * y;
+            bq[i] = sn * x + c * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();                     // everyone has read `rotated` before it is reset
+  }
+  for (long long e = tid; e < (long long)m * ell; e += kJT) {
+    const int i = (int)(e % m), c = (int)(e / m);
+    B[(size_t)c * ld + i] = M[e];
+  }
+  if (tid == 0) *sweeps_out = sweep < max_sweeps ? sweep + 1 : max_sweeps + 1;
 }
 
 // G[j][j] += f * trace(G)  (one CTA): the shift of the first Cholesky-QR pass.
@@ -240,6 +432,36 @@ __global__ void k_normalise(int m, int ell, const double* __restrict__ B, int ld
   U[(size_t)r * ld + i] = B[(size_t)j * ld + i] * inv;
 }
 
+// Cholesky of the ell x ell core (shared memory when it fits).
+cudaError_t launch_chol(cudaStream_t st, int ell, double* G, int* err) {
+  count_launches(1);
+  if (ell <= kCholSmemMax) {
+    const size_t sm = sizeof(double) * (size_t)ell * ell;
+    cudaError_t e = cudaFuncSetAttribute(k_chol_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * kCholSmemMax * kCholSmemMax));
+    if (e != cudaSuccess) return e;
+    k_chol_smem<<<1, kNT, sm, st>>>(ell, G, err);
+  } else {
+    k_chol<<<1, kNT, 0, st>>>(ell, G, err);
+  }
+  return cudaGetLastError();
+}
+
+// B = B C^{-1} for an m x ell B (column-major, ld) and upper-triangular C.
+cudaError_t launch_trsm(cudaStream_t st, int m, int ell, double* B, int ld, const double* C, int* err) {
+  count_launches(1);
+  if (ell <= kTrsmSmemMax) {
+    const size_t sm = sizeof(double) * ((size_t)ell * kTrsmRows + ell);
+    cudaError_t e = cudaFuncSetAttribute(k_trsm_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * ((size_t)kTrsmSmemMax * kTrsmRows + kTrsmSmemMax)));
+    if (e != cudaSuccess) return e;
+    k_trsm_smem<<<(m + kTrsmRows - 1) / kTrsmRows, kTrsmRows, sm, st>>>(m, ell, B, ld, C, err);
+  } else {
+    k_trsm_rows<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, ell, B, ld, C, err);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, const double* Om,
@@ -258,15 +480,16 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   cudaError_t e = gemm_f64(st, ell, ell, m, Om, ld, 1, cw.Ynu, 1, ld, nullptr, cw.G, 1, ell,
                            cw.split_buf, cw.split_cap);
   if (e != cudaSuccess) return e;
-  count_launches(1);
-  k_chol<<<1, kNT, 0, st>>>(ell, cw.G, err);
-  count_launches(1);
-  k_trsm_rows<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, ell, cw.Ynu, ld, cw.G, err);
+  e = launch_chol(st, ell, cw.G, err);
+  if (e != cudaSuccess) return e;
+  e = launch_trsm(st, m, ell, cw.Ynu, ld, cw.G, err);
+  if (e != cudaSuccess) return e;
   double* Bsv = cw.Ynu;           // matrix whose column norms / directions give U and Sigma
   int jm = m, jld = ld;           // Jacobi problem: rows and leading dimension
   double* Jmat = cw.Ynu;
-  if (ell > kJacobiDirectMaxEll) {
-    // Large ell: B = Q R by a shifted three-pass Cholesky QR (the first pass
+  const bool direct = m <= 2 * ell && (long long)m * ell <= kJacobiSmemElems;
+  if (!direct) {
+    // B = Q R by a shifted three-pass Cholesky QR (the first pass
     // shifted by 1e-10 trace(B^T B) so it cannot break down), then the SVD of
     // the small ell x ell R by one-sided Jacobi, W = R V, and B V = Q W.
     for (int pass = 0; pass < 3; ++pass) {
@@ -277,10 +500,10 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
         count_launches(1);
         k_shift_trace<<<1, kNT, 0, st>>>(ell, cw.G, 1e-10);
       }
-      count_launches(1);
-      k_chol<<<1, kNT, 0, st>>>(ell, cw.G, err);
-      count_launches(1);
-      k_trsm_rows<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, ell, cw.Ynu, ld, cw.G, err);
+      e = launch_chol(st, ell, cw.G, err);
+      if (e != cudaSuccess) return e;
+      e = launch_trsm(st, m, ell, cw.Ynu, ld, cw.G, err);
+      if (e != cudaSuccess) return e;
       const unsigned sb = (unsigned)(((long long)ell * ell + kNT - 1) / kNT);
       if (pass == 0) {
         cudaMemcpyAsync(cw.R, cw.G, sizeof(double) * ell * ell, cudaMemcpyDeviceToDevice, st);
@@ -294,27 +517,39 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
     jm = ell;
     jld = ell;
   }
-  // one-sided Jacobi (cooperative)
-  cudaMemsetAsync(cw.sweep_flags, 0, sizeof(int) * CoreWork::kMaxSweeps, st);
-  cudaMemsetAsync(cw.bar, 0, 2 * sizeof(unsigned), st);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kNT, 0);
-  int grid = (ell + 1) / 2;
-  const int cap = per_sm * num_sms;
-  if (grid > cap) grid = cap;
-  if (grid < 1) grid = 1;
   double tol = sqrt((double)jm) * 0x1.0p-53;
   if (tol < 0x1.0p-52) tol = 0x1.0p-52;
-  int mm = jm, ee = ell, ldd = jld, ms = CoreWork::kMaxSweeps;
-  double* Bp = Jmat;
-  int* flags = cw.sweep_flags;
-  unsigned* bar = cw.bar;
-  int* sweeps = si + SI_SWEEPS;
-  void* args[] = {&mm, &ee, &Bp, &ldd, &tol, &flags, &ms, &bar, &err, &sweeps};
-  count_launches(1);
-  e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kNT), args, 0, st);
+  if ((long long)jm * ell <= kJacobiSmemElems) {
+    // one-sided Jacobi in one CTA's shared memory
+    const size_t sm = sizeof(double) * (size_t)jm * ell;
+    // the attribute is set to the kernel's maximum, never lowered: handles on
+    // other host threads may be launching it concurrently
+    e = cudaFuncSetAttribute(k_jacobi_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * kJacobiSmemElems));
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_jacobi_smem<<<1, kJT, sm, st>>>(jm, ell, Jmat, jld, tol, CoreWork::kMaxSweeps, err, si + SI_SWEEPS);
+  } else {
+    // one-sided Jacobi (cooperative)
+    cudaMemsetAsync(cw.sweep_flags, 0, sizeof(int) * CoreWork::kMaxSweeps, st);
+    cudaMemsetAsync(cw.bar, 0, 2 * sizeof(unsigned), st);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kNT, 0);
+    int grid = (ell + 1) / 2;
+    const int cap = per_sm * num_sms;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    int mm = jm, ee = ell, ldd = jld, ms = CoreWork::kMaxSweeps;
+    double* Bp = Jmat;
+    int* flags = cw.sweep_flags;
+    unsigned* bar = cw.bar;
+    int* sweeps = si + SI_SWEEPS;
+    void* args[] = {&mm, &ee, &Bp, &ldd, &tol, &flags, &ms, &bar, &err, &sweeps};
+    count_launches(1);
+    e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kNT), args, 0, st);
+  }
   if (e != cudaSuccess) return e;
-  if (ell > kJacobiDirectMaxEll) {
+  if (!direct) {
     // B V = Q W  (m x ell times ell x ell)
     e = gemm_f64(st, m, ell, ell, cw.Ynu, 1, ld, cw.R, 1, ell, nullptr, cw.B2, 1, ld, cw.split_buf,
                  cw.split_cap);

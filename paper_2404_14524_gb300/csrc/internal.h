@@ -191,6 +191,30 @@ cudaError_t pcg_persistent_f64(cudaStream_t st, int m, int n, const double* A, l
                                double delta, int ell, const double* U, int ld, const double* lam, const double* xi,
                                double eta, int max_iter, int forced, PcgWork w, double* part, size_t part_cap,
                                unsigned* bar, double* sd, int* si, int num_sms);
+// Whole PCG solves in thread-block clusters (small problems): one cluster of
+// C CTAs per system, the column band of A in shared memory when it fits.
+struct ClusterPcgTask {
+  int m, n, ell, ld;
+  long long lda;
+  const double *A, *D, *U, *lam, *xi;   // device: m x n (lda), n, m x ell (ld), ell, m
+  double delta, eta2;
+  int max_iter, forced;
+  double* x;                            // device, m: the solution
+  int* iters;                           // device: iterations taken
+  double* sd;                           // device scalars: SD_RR, SD_BNORM2, SD_ETA2 written
+  int* err;                             // device error word
+};
+struct ClusterPlan {
+  int C = 0;                            // CTAs per cluster (8 or 16)
+  int a_smem = 0;                       // A's column band held in shared memory
+  size_t smem_bytes = 0;                // dynamic shared memory per CTA
+};
+// Plan for an m x n system with rank ell; false when no cluster fits.
+bool pcg_cluster_plan(int m, int n, int ell, ClusterPlan* plan);
+// One system (`task`, tasks == nullptr) or `count` systems from the device
+// array `tasks`, each planned no larger than `plan`.
+cudaError_t pcg_cluster_f64(cudaStream_t st, const ClusterPlan& plan, const ClusterPcgTask& task,
+                            const ClusterPcgTask* tasks, int count);
 // Body-graph tail of a conditional while node: keep looping while !SI_DONE.
 cudaError_t pcg_loop_condition(cudaStream_t st, cudaGraphConditionalHandle cond, const int* si);
 

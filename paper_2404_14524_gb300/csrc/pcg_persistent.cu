@@ -30,6 +30,7 @@ constexpr int kPT = 256;
 constexpr int kPW = kPT / 32;
 constexpr int kMaxM = 4096;      // p lives in shared memory
 constexpr int kMaxEll = 1024;
+constexpr int kMaxSmemVec = 24576;   // m + n entries of p and t in shared memory
 
 struct PState {
   double *x, *r, *z, *w, *t;
@@ -93,7 +94,8 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
                                                         const double* __restrict__ lam, const double* __restrict__ xi,
                                                         PState S, double eta2, int max_iter, int forced,
                                                         unsigned* bar, int* err, int* iters_out, double* sd) {
-  extern __shared__ double ps[];            // p, m entries
+  extern __shared__ double ps[];            // p (m entries), then t (n entries)
+  double* ts = ps + m;
   __shared__ double sh[kPW * 4 + 2];
   __shared__ double ws[kMaxEll];            // (lam_ell + delta) / (lam + delta) - 1
   __shared__ double ss[kMaxEll];            // s = U^T r
@@ -147,12 +149,16 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
     }
     __threadfence();
     if (!grid_barrier(bar, err)) return;
-    // 2. w = A t + delta p over own rows (warp per row); p^T w
+    // 2. w = A t + delta p over own rows (warp per row); p^T w.  t is staged
+    // in shared memory first (one coalesced pass instead of a chain of L2
+    // round trips per row).
+    for (int j = tid; j < n; j += kPT) ts[j] = __ldcg(S.t + j);
+    __syncthreads();
     double v = 0.0;
     for (int i = i0 + wid; i < i1; i += kPW) {
       const double* a = A + (long long)i * lda;
       double acc = 0.0;
-      for (int j = lane; j < n; j += 32) acc = fma(__ldg(a + j), __ldcg(S.t + j), acc);
+      for (int j = lane; j < n; j += 32) acc = fma(__ldg(a + j), ts[j], acc);
       acc = warp_sum(acc);
       if (lane == 0) {
         const double wi = fma(delta, ps[i], acc);
@@ -202,15 +208,19 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
 }  // namespace
 
 bool pcg_persistent_fits(int m, int n, int ell) {
-  return m <= kMaxM && (long long)m * n <= (1ll << 23) && ell <= kMaxEll;
+  // p and t in shared memory next to the 16 KB of weights and U^T r
+  return m <= kMaxM && m + n <= kMaxSmemVec && (long long)m * n <= (1ll << 23) && ell <= kMaxEll;
 }
 
 cudaError_t pcg_persistent_f64(cudaStream_t st, int m, int n, const double* A, long long lda, const double* D,
                                double delta, int ell, const double* U, int ld, const double* lam, const double* xi,
                                double eta, int max_iter, int forced, PcgWork w, double* part, size_t part_cap,
                                unsigned* bar, double* sd, int* si, int num_sms) {
-  const size_t dsm = sizeof(double) * (size_t)m;
-  cudaError_t e = cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+  const size_t dsm = sizeof(double) * ((size_t)m + (size_t)n);
+  // set to the kernel's maximum (p and t of the largest fitting system), never
+  // lowered: handles on other host threads may be launching it concurrently
+  cudaError_t e = cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * kMaxSmemVec));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kPT, dsm);

@@ -2,10 +2,10 @@
 // (Algorithm 1, first two steps).
 //
 // The FP64 sketch is two SIMT DFMA GEMMs (GB300 has no FP64 tensor-core
-// kind for tcgen05, and its DFMA rate is the bound): 64x64 output tiles,
-// 16-deep k-slices staged in shared memory, 4x4 register blocking per thread,
-// split-K with a fixed-order reduction when there are too few output tiles to
-// fill the 152 SMs.
+// kind for tcgen05, and its DFMA rate is the bound): 64x64 output tiles (32x32
+// when the sketch has at most 32 columns), 16-deep k-slices staged in shared
+// memory, register blocking per thread, split-K with a fixed-order reduction
+// when there are too few output tiles to fill the 152 SMs.
 #include "common.cuh"
 #include "internal.h"
 
@@ -38,41 +38,46 @@ __global__ void k_gaussian(unsigned long long seed, int k, int m, int ell, doubl
 }
 
 // ---- FP64 SIMT GEMM
-constexpr int BM = 64, BN = 64, BK = 16;
+// TBM x TBN output tiles (64 x 64, or 32 x 32 for the skinny products of a
+// small sketch, so that few DFMAs go to padding), 16-deep k-slices staged in
+// shared memory, (TBM/16) x (TBN/16) outputs per thread.
+constexpr int BK = 16;
 
-template <bool kAK>  // kAK: A's k index is contiguous (sak == 1); else r is (sar == 1)
+template <bool kAK, int TBM, int TBN>  // kAK: A's k index is contiguous (sak == 1); else r is (sar == 1)
 __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, int kchunk,
                                                   const double* __restrict__ A, long long sar,
                                                   long long sak, const double* __restrict__ B,
                                                   long long sbc, const double* __restrict__ scale,
                                                   double* __restrict__ C, long long scr,
                                                   long long scc, double* __restrict__ part) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  constexpr int RM = TBM / 16, RN = TBN / 16;   // outputs per thread
+  constexpr int EA = BK * TBM / 256, EB = BK * TBN / 256;
+  __shared__ double As[BK][TBM + 1];
+  __shared__ double Bs[BK][TBN + 1];
   const int tid = threadIdx.x;
-  const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
+  const int r0 = blockIdx.x * TBM, c0 = blockIdx.y * TBN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const int tr = tid >> 4, tc = tid & 15;
-  double acc[4][4];
+  double acc[RM][RN];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RM; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < RN; ++b) acc[a][b] = 0.0;
 
   for (int kk = kbeg; kk < kend; kk += BK) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < EA; ++e) {
       const int idx = tid + e * 256;
       int r, k;
-      if (kAK) { r = idx / BK; k = idx % BK; } else { r = idx % BM; k = idx / BM; }
+      if (kAK) { r = idx / BK; k = idx % BK; } else { r = idx % TBM; k = idx / TBM; }
       const int gr = r0 + r, gk = kk + k;
       double val = 0.0;
       if (gr < M && gk < kend) val = __ldg(A + (long long)gr * sar + (long long)gk * sak);
       As[k][r] = val;
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < EB; ++e) {
       const int idx = tid + e * 256;
       const int k = idx % BK, c = idx / BK;
       const int gk = kk + k, gc = c0 + c;
@@ -86,23 +91,25 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, int kchun
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
+      double a[RM], b[RN];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) { a[t] = As[k][tr * 4 + t]; b[t] = Bs[k][tc * 4 + t]; }
+      for (int t = 0; t < RM; ++t) a[t] = As[k][tr * RM + t];
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int t = 0; t < RN; ++t) b[t] = Bs[k][tc * RN + t];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+      for (int x = 0; x < RM; ++x)
+#pragma unroll
+        for (int y = 0; y < RN; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int gr = r0 + tr * 4 + x;
+  for (int x = 0; x < RM; ++x) {
+    const int gr = r0 + tr * RM + x;
     if (gr >= M) continue;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int gc = c0 + tc * 4 + y;
+    for (int y = 0; y < RN; ++y) {
+      const int gc = c0 + tc * RN + y;
       if (gc >= N) continue;
       if (part) part[(size_t)blockIdx.z * M * N + (size_t)gc * M + gr] = acc[x][y];
       else C[(long long)gr * scr + (long long)gc * scc] = acc[x][y];
@@ -137,22 +144,34 @@ cudaError_t gemm_f64(cudaStream_t st, int M, int N, int K, const double* A, long
                      double* split_buf, size_t split_cap) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (sbk != 1 || (sar != 1 && sak != 1)) return cudaErrorInvalidValue;
-  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  // small N (a sketch of rank <= 32): 32 x 32 tiles
+  const bool skinny = N <= 32;
+  const int tbm = skinny ? 32 : 64, tbn = skinny ? 32 : 64;
+  const int tiles = ((M + tbm - 1) / tbm) * ((N + tbn - 1) / tbn);
   const int ksteps = (K + BK - 1) / BK;
+  // split K until the grid covers the GPU about four times (each split keeps
+  // at least two 16-deep slices), within the partial-sum scratch
   int S = (152 * 4 + tiles - 1) / tiles;
-  if (S > ksteps / 4) S = ksteps / 4;
+  if (S > ksteps / 2) S = ksteps / 2;
   if (S < 1) S = 1;
   while (S > 1 && (size_t)S * M * N > split_cap) --S;
   const int kchunk = ((ksteps + S - 1) / S) * BK;
   S = (K + kchunk - 1) / kchunk;
   if (S < 1) S = 1;
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, S);
+  dim3 grid((M + tbm - 1) / tbm, (N + tbn - 1) / tbn, S);
   double* part = (S > 1) ? split_buf : nullptr;
   count_launches(1);
-  if (sak == 1)
-    k_gemm_f64<true><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, sar, sak, B, sbc, scale, C, scr, scc, part);
-  else
-    k_gemm_f64<false><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, sar, sak, B, sbc, scale, C, scr, scc, part);
+  if (skinny) {
+    if (sak == 1)
+      k_gemm_f64<true, 32, 32><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, sar, sak, B, sbc, scale, C, scr, scc, part);
+    else
+      k_gemm_f64<false, 32, 32><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, sar, sak, B, sbc, scale, C, scr, scc, part);
+  } else {
+    if (sak == 1)
+      k_gemm_f64<true, 64, 64><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, sar, sak, B, sbc, scale, C, scr, scc, part);
+    else
+      k_gemm_f64<false, 64, 64><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, sar, sak, B, sbc, scale, C, scr, scc, part);
+  }
   if (S > 1) {
     const long long total = (long long)M * N;
     count_launches(1);

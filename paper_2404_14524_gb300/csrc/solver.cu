@@ -63,6 +63,9 @@ struct nys_solver {
   // PCG as one graph launch: a conditional while node whose body is one
   // predicated iteration (rebuilt when the operator's pointers change)
   cudaStream_t cap_stream = nullptr;
+  // device time of the PCG solves: events around each solve on the stream
+  cudaEvent_t ev_pcg0 = nullptr, ev_pcg1 = nullptr;
+  double pcg_ms = 0.0;
   cudaGraph_t pcg_graph = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
   const void* gk_A = nullptr;
@@ -71,7 +74,12 @@ struct nys_solver {
   int gk_m = 0, gk_n = 0, gk_ell = 0, gk_ld = 0;
   unsigned g_kernels_per_iter = 0;
   bool use_graphs = true;
-  bool use_persistent = true;   // one cooperative launch per PCG solve for small problems
+  // FP64 PCG route: 0 by size (cluster, else cooperative, else graph),
+  // 1 cluster only, 2 cooperative only, 3 graph only (NYS_PCG_PATH)
+  int pcg_path = 0;
+  int cp_m = -1, cp_n = -1, cp_ell = -1;   // key of the cached cluster plan
+  bool cp_ok = false;
+  ClusterPlan cp;
   int gk_op = -1;            // graph key: operator kind
   double* pcg_x = nullptr;   // PCG solution buffer (copied out after each solve)
   // precision form (precision_mode 1): A is FP32 (the problem definition);
@@ -336,19 +344,39 @@ bool ensure_pcg_graph(nys_solver* h, int m, int n, const OpSpec& op, int ell, co
   return true;
 }
 
+// Route of an FP64 PCG solve (NYS_ROUTE_*): a thread-block cluster when a
+// cluster plan exists, else one cooperative launch when it fits, else the
+// graph of per-step kernels; NYS_PCG_PATH restricts the choice.
+int fp64_route(nys_solver* h, int m, int n, int ell) {
+  if (h->cp_m != m || h->cp_n != n || h->cp_ell != ell) {
+    h->cp_ok = pcg_cluster_plan(m, n, ell, &h->cp);
+    h->cp_m = m; h->cp_n = n; h->cp_ell = ell;
+  }
+  if ((h->pcg_path == 0 || h->pcg_path == 1) && h->cp_ok)
+    return h->cp.a_smem ? NYS_ROUTE_CLUSTER_SMEM : NYS_ROUTE_CLUSTER_L2;
+  if ((h->pcg_path == 0 || h->pcg_path == 2) && pcg_persistent_fits(m, n, ell)) return NYS_ROUTE_COOPERATIVE;
+  return NYS_ROUTE_GRAPH;
+}
+
 // Run PCG on (A D A^T + delta I) dy = xi; dy is written into `out`.
 int run_pcg(nys_solver* h, int m, int n, const OpSpec& op, double delta, int ell, const double* U, int ld,
             const double* lamh, const double* xi, double* out, double eta, int max_iter, int forced,
             int* iters) {
   PcgWork w = h->pw;
   w.x = h->pcg_x;
-  if (op.kind == 0 && h->use_persistent && pcg_persistent_fits(m, n, ell)) {
-    // small problem: the whole solve in one cooperative launch
-    CK(pcg_persistent_f64(h->st, m, n, op.A, op.lda, op.D, delta, ell, U, ld, lamh, xi, eta, max_iter, forced,
-                          w, h->red.part, RedBuf::kPartCap, h->cw.bar, h->sd, h->si, h->num_sms));
-    CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaEventRecord(h->ev_pcg0, h->st));
+  // after the stream has been synchronised: add this solve's device time
+  auto add_time = [&]() {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pcg0, h->ev_pcg1) == cudaSuccess) h->pcg_ms += ms;
+    else cudaGetLastError();
+  };
+  // one-launch routes: report the count and whether the stop test was met
+  auto finish_single = [&]() -> int {
+    CK(cudaEventRecord(h->ev_pcg1, h->st));
     int rc = sync_scalars(h, 0);
     if (rc != NYS_OK) return rc;
+    add_time();
     *iters = h->h_si[SI_ITERS];
     if (forced < 0 && *iters >= max_iter) {
       CK(cudaMemcpyAsync(h->h_red, h->sd, sizeof(double) * SD_COUNT, cudaMemcpyDeviceToHost, h->st));
@@ -356,14 +384,34 @@ int run_pcg(nys_solver* h, int m, int n, const OpSpec& op, double delta, int ell
       if (!(h->h_red[SD_RR] <= h->h_red[SD_ETA2] * h->h_red[SD_BNORM2])) return NYS_WARN_PCG_MAXITER;
     }
     return NYS_OK;
+  };
+  const int route = op.kind == 0 ? fp64_route(h, m, n, ell) : NYS_ROUTE_GRAPH;
+  if (route == NYS_ROUTE_CLUSTER_SMEM || route == NYS_ROUTE_CLUSTER_L2) {
+    // small problem: the whole solve inside one thread-block cluster
+    ClusterPcgTask t{};
+    t.m = m; t.n = n; t.ell = ell; t.ld = ld; t.lda = op.lda;
+    t.A = op.A; t.D = op.D; t.U = U; t.lam = lamh; t.xi = xi;
+    t.delta = delta; t.eta2 = eta * eta; t.max_iter = max_iter; t.forced = forced;
+    t.x = out; t.iters = h->si + SI_ITERS; t.sd = h->sd; t.err = h->si + SI_ERR;
+    CK(pcg_cluster_f64(h->st, h->cp, t, nullptr, 1));
+    return finish_single();
+  }
+  if (route == NYS_ROUTE_COOPERATIVE) {
+    // small problem: the whole solve in one cooperative launch
+    CK(pcg_persistent_f64(h->st, m, n, op.A, op.lda, op.D, delta, ell, U, ld, lamh, xi, eta, max_iter, forced,
+                          w, h->red.part, RedBuf::kPartCap, h->cw.bar, h->sd, h->si, h->num_sms));
+    CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    return finish_single();
   }
   CK(pcg_setup_f64(h->st, m, ell, U, ld, lamh, delta, xi, eta, max_iter, forced, w, h->sd, h->si, h->red));
   const int limit = forced >= 0 ? forced : max_iter;
   if (ensure_pcg_graph(h, m, n, op, ell, U, ld)) {
     CK(cudaGraphLaunch(h->pcg_exec, h->st));
+    CK(cudaEventRecord(h->ev_pcg1, h->st));
     CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
     int rc = sync_scalars(h, 0);
     if (rc != NYS_OK) return rc;
+    add_time();
     const int it = h->h_si[SI_ITERS];
     count_launches(h->g_kernels_per_iter * (unsigned)std::max(it, 1));
   } else {
@@ -377,6 +425,9 @@ int run_pcg(nys_solver* h, int m, int n, const OpSpec& op, double delta, int ell
       issued += todo;
       chunk = std::min(chunk * 2, 16);
     }
+    CK(cudaEventRecord(h->ev_pcg1, h->st));
+    CK(cudaEventSynchronize(h->ev_pcg1));
+    add_time();
     CK(cudaMemcpyAsync(out, w.x, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
   }
   *iters = h->h_si[SI_ITERS];
@@ -638,13 +689,17 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
     carve_lp(h, static_cast<char*>(h->lp_arena));
     cudaMemsetAsync(h->lp_arena, 0, h->lp_bytes, h->st);
   }
-  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&h->ev_pcg0) != cudaSuccess || cudaEventCreate(&h->ev_pcg1) != cudaSuccess) {
     cudaFree(h->arena);
     delete h;
     return NYS_ERR_CUDA;
   }
   if (const char* env = std::getenv("NYS_NO_GRAPHS")) h->use_graphs = (env[0] == '0');
-  if (const char* env = std::getenv("NYS_PCG_PERSISTENT")) h->use_persistent = (env[0] != '0');
+  if (const char* env = std::getenv("NYS_PCG_PATH")) {
+    const std::string v(env);
+    h->pcg_path = v == "cluster" ? 1 : v == "cooperative" ? 2 : v == "graph" ? 3 : 0;
+  }
   if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess) {
@@ -664,6 +719,8 @@ int nys_destroy(nys_handle h) {
   else cudaDeviceSynchronize();
   drop_pcg_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->ev_pcg0) cudaEventDestroy(h->ev_pcg0);
+  if (h->ev_pcg1) cudaEventDestroy(h->ev_pcg1);
   cudaFree(h->arena);
   if (h->lp_arena) cudaFree(h->lp_arena);
   if (h->stage) cudaFree(h->stage);
@@ -881,6 +938,11 @@ int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result*
   return worst;
 }
 
+int nys_pcg_route(nys_handle h, int m, int n, int ell) {
+  if (!h || m <= 0 || n <= 0 || ell <= 0) return NYS_ERR_ARG;
+  return fp64_route(h, m, n, ell);
+}
+
 int nys_gemm_bf16(nys_handle h, int M, int N, int K, const void* A, long long lda, const void* B,
                   long long ldb, float* C, long long ldc) {
   if (!h) return NYS_ERR_ARG;
@@ -927,6 +989,8 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   r->pcg_iters_total = 0;
   r->refine_steps = 0;
   r->pcg_log_len = 0;
+  r->pcg_seconds = 0.0;
+  h->pcg_ms = 0.0;
 
   // Problem data on the device (staged when the caller passes host memory).
   const size_t esz = lp ? sizeof(float) : sizeof(double);
@@ -1128,6 +1192,7 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   if (status >= 0 && h->h_red[7] != 0.0) status = fail(h, NYS_ERR_NUMERIC, "non-finite final iterate");
   r->status = status;
   r->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r->pcg_seconds = h->pcg_ms * 1e-3;
   return status;
 }
 

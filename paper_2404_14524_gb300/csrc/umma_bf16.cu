@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kBM = 128;        // rows per CTA (UMMA M)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = 128 bytes = one swizzle atom row
+constexpr int kMaxDynSmem = 227 * 1024;   // opt-in shared memory per CTA
 constexpr int kUmmaK = 16;      // K per tcgen05.mma for kind::f16
 constexpr int kThreads = 128;
 constexpr unsigned kTmemCols = 512;
@@ -335,19 +336,22 @@ cudaError_t umma_gemm_bf16(cudaStream_t st, int M, int N, int K, const void* A, 
   cudaError_t e;
   if (npad <= 128) {
     const size_t sm = smem_bytes<6>(npad);
-    e = cudaFuncSetAttribute(k_umma_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(k_umma_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxDynSmem);   // never lowered: other host threads may launch it
     if (e != cudaSuccess) return e;
     count_launches(1);
     k_umma_gemm<6><<<grid, kThreads, sm, st>>>(ma, mb, M, npad, br, K, per, part, err);
   } else if (npad <= 256) {
     const size_t sm = smem_bytes<4>(npad);
-    e = cudaFuncSetAttribute(k_umma_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(k_umma_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxDynSmem);   // never lowered: other host threads may launch it
     if (e != cudaSuccess) return e;
     count_launches(1);
     k_umma_gemm<4><<<grid, kThreads, sm, st>>>(ma, mb, M, npad, br, K, per, part, err);
   } else {
     const size_t sm = smem_bytes<3>(npad);
-    e = cudaFuncSetAttribute(k_umma_gemm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(k_umma_gemm<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxDynSmem);   // never lowered: other host threads may launch it
     if (e != cudaSuccess) return e;
     count_launches(1);
     k_umma_gemm<3><<<grid, kThreads, sm, st>>>(ma, mb, M, npad, br, K, per, part, err);

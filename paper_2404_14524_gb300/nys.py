@@ -66,7 +66,7 @@ class Result(ctypes.Structure):
                 ("rel_primal", ctypes.c_double), ("rel_dual", ctypes.c_double),
                 ("mu", ctypes.c_double), ("rel_gap", ctypes.c_double), ("rho", ctypes.c_double),
                 ("delta", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
+                ("pcg_seconds", ctypes.c_double), ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
                 ("pcg_log_len", ctypes.c_int)]
 
 
@@ -83,6 +83,7 @@ _SIGS = {
     "nys_destroy": (_I, [_P]),
     "nys_last_error": (ctypes.c_char_p, [_P]),
     "nys_kernel_launches": (ctypes.c_ulonglong, []),
+    "nys_pcg_route": (_I, [_P, _I, _I, _I]),
     "nys_scaling": (_I, [_P, _I, _P, _P, _P, _D, _P]),
     "nys_normal_matvec": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _P, _P]),
     "nys_normal_matvec_lp": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _D, _P, _P]),
@@ -205,6 +206,18 @@ def nys_last_error(h: Handle) -> str:
 
 def nys_kernel_launches() -> int:
     return int(lib().nys_kernel_launches())
+
+
+NYS_ROUTE_CLUSTER_SMEM, NYS_ROUTE_CLUSTER_L2, NYS_ROUTE_COOPERATIVE, NYS_ROUTE_GRAPH = 0, 1, 2, 3
+ROUTE_NAMES = {0: "cluster-smem", 1: "cluster-l2", 2: "cooperative", 3: "graph"}
+
+
+def nys_pcg_route(h, m: int, n: int, ell: int) -> int:
+    """Route (NYS_ROUTE_*) an FP64 PCG solve of this size takes on this handle."""
+    rc = int(lib().nys_pcg_route(h.h, m, n, ell))
+    if rc < 0:
+        raise NysError(rc, "nys_pcg_route: bad argument")
+    return rc
 
 
 def nys_scaling(h: Handle, x, z, q, rho: float, D=None):
@@ -370,7 +383,7 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
         h.check(rc)
     info = {k: getattr(r, k) for k in ("status", "ipm_iters", "pcg_iters_total", "refine_steps",
                                        "rel_primal", "rel_dual", "mu", "rel_gap", "rho", "delta",
-                                       "seconds")}
+                                       "seconds", "pcg_seconds")}
     info["pcg_log"] = list(log[: r.pcg_log_len])
     if want_pmm:
         info["lam"], info["zeta"] = lam, zeta
@@ -447,6 +460,7 @@ def nys_solve_batched(h: Handle, problems, check: bool = True):
     res = []
     for i, (x, y, z) in enumerate(outs):
         info = {f: getattr(R[i], f) for f in ("status", "ipm_iters", "pcg_iters_total", "refine_steps", "rel_primal",
-                                              "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds")}
+                                              "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds",
+                                              "pcg_seconds")}
         res.append((x, y, z, info))
     return res

@@ -121,10 +121,12 @@ def _factor_pair(nys, m, n, ell, seed, rank=None, dscale=1.0):
 
 
 @pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (301, 450, 47), (64, 64, 64), (5, 9, 1),
-                                     (600, 900, 120), (1000, 1500, 201)])
+                                     (1024, 1500, 32), (600, 900, 120), (1000, 1500, 201)])
 def test_nystrom_factor_matches_oracle(nys, m, n, ell):
-    """Small ell: one-sided Jacobi on B; ell > 96: QR of B first (shifted
-    Cholesky QR3) and Jacobi on the ell x ell factor."""
+    """ell <= 96 with m ell <= 25600: one-sided Jacobi on B in one CTA's
+    shared memory; otherwise QR of B first (shifted Cholesky QR3) and Jacobi
+    on the ell x ell factor (in shared memory up to ell = 160, else the
+    cooperative kernel)."""
     h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, m, n, ell, seed=m + ell)
     assert nu == Fw.nu
     assert np.all(np.diff(lam) <= 0) and np.all(lam >= 0)
@@ -296,9 +298,13 @@ def test_single_ipm_step_matches_oracle(nys, small_run, k):
     errs = [relerr(g, w) for g, w in ((gx, want[0]), (gy, want[1]), (gz, want[2]))]
     print(f"k={k} errs={errs} floor={floor:.2e}")
     assert max(errs) <= tol
-    if nxt is not None:    # PEU after the step (r_mu inherits the iterate's noise floor)
-        assert abs(info["rho"] - nxt.rho) <= tol * nxt.rho
-        assert abs(info["delta"] - nxt.delta) <= tol * nxt.delta
+    if nxt is not None:
+        # PEU after the step: rho' = (1 - r_mu) rho with r_mu = |mu' - mu| / max(mu', mu).
+        # mu' = x'^T z' / n carries up to twice the iterate's relative error, which
+        # moves r_mu by as much in absolute terms and rho' by that over (1 - r_mu).
+        tol_reg = 2 * tol / (nxt.rho / t.rho)
+        assert abs(info["rho"] - nxt.rho) <= tol_reg * nxt.rho
+        assert abs(info["delta"] - nxt.delta) <= tol_reg * nxt.delta
 
 
 def test_small_workload_solution_matches_oracle(nys, small_run):
@@ -374,16 +380,27 @@ def test_core_breakdown_is_reported_not_trapped(nys):
     assert torch.isfinite(out).all()
 
 
-def test_persistent_pcg_matches_the_graph_pcg(nys, monkeypatch):
-    """Small systems run the whole PCG in one cooperative launch; it must give
-    the same solution as the multi-kernel (CUDA graph) path."""
-    h1, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, 300, 900, 24, seed=21)
-    xi = np.random.default_rng(4).standard_normal(300)
-    monkeypatch.setenv("NYS_PCG_PERSISTENT", "0")
-    h0 = nys.Handle(300, 900, ell=24)
-    monkeypatch.delenv("NYS_PCG_PERSISTENT")
+@pytest.mark.parametrize("m,n,ell,path,route", [
+    (300, 900, 24, "cluster", 0),       # A's column bands in shared memory
+    (7, 41, 3, "cluster", 0),           # fewer rows and columns than CTAs
+    (700, 1400, 16, "cluster", 1),      # A read from L2 by the cluster
+    (300, 900, 24, "cooperative", 2),   # grid-wide cooperative launch
+])
+def test_one_launch_pcg_routes_match_the_graph_pcg(nys, monkeypatch, m, n, ell, path, route):
+    """Small systems run the whole PCG in one launch (a thread-block cluster,
+    or one cooperative grid); each route must give the multi-kernel (CUDA
+    graph) path's solution up to summation order."""
+    h1, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, m, n, ell, seed=21)
+    xi = np.random.default_rng(4).standard_normal(m)
+    monkeypatch.setenv("NYS_PCG_PATH", path)
+    hr = nys.Handle(m, n, ell=ell)
+    monkeypatch.setenv("NYS_PCG_PATH", "graph")
+    h0 = nys.Handle(m, n, ell=ell)
+    monkeypatch.delenv("NYS_PCG_PATH")
+    assert nys.nys_pcg_route(hr, m, n, ell) == route
+    assert nys.nys_pcg_route(h0, m, n, ell) == nys.NYS_ROUTE_GRAPH
     for forced in (5, -1):
-        a, ia, ra, _ = nys.nys_pcg(h1, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
+        a, ia, ra, _ = nys.nys_pcg(hr, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
         b, ib, rb, _ = nys.nys_pcg(h0, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
         assert abs(ia - ib) <= (0 if forced >= 0 else 1)
         assert relerr(a, b.cpu().numpy()) <= (1e-11 if forced >= 0 else 1e-7)
