@@ -254,7 +254,9 @@ int nys_pcg(nys_handle h, int m, int n, int a_dtype, const void* A, long long ld
  *   NYS_ROUTE_COOPERATIVE   one cooperative grid-wide launch;
  *   NYS_ROUTE_GRAPH         one CUDA-graph launch of per-step kernels.
  * The choice depends only on (m, n, ell), the device and the environment
- * variable NYS_PCG_PATH (cluster | cooperative | graph) read at nys_create.
+ * variable NYS_PCG_PATH (cluster | cooperative | graph) read at nys_create
+ * (with "cluster", systems whose A does not fit on chip use a cluster that
+ * reads A from L2).
  * Returns the route, or NYS_ERR_ARG for a null handle or sizes <= 0.
  * The paper has no counterpart: its PCG runs on a CPU. */
 enum { NYS_ROUTE_CLUSTER_SMEM = 0, NYS_ROUTE_CLUSTER_L2 = 1, NYS_ROUTE_COOPERATIVE = 2, NYS_ROUTE_GRAPH = 3 };

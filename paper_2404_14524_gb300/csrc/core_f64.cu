@@ -17,6 +17,8 @@
 // ell.  Matrices of up to 25600 entries are rotated by a single CTA in shared
 // memory (__syncthreads between rounds); larger ones by the cooperative
 // kernel with grid barriers.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -371,6 +373,153 @@ __global__ void __launch_bounds__(kJT) k_jacobi_smem(int m, int ell, double* B, 
   if (tid == 0) *sweeps_out = sweep < max_sweeps ? sweep + 1 : max_sweeps + 1;
 }
 
+// The same Jacobi iteration on a thread-block cluster, for ell <= 32: the
+// rounds are latency chains of FP64 divisions and roots (hundreds of cycles
+// each on this GPU), so each of the ceil(ell/2) pairs of a round gets its own
+// CTA.  CTA k holds the two columns of pair k of the current round in shared
+// memory (double-buffered), rotates them (all threads over the rows, one
+// thread for the rotation), and after the round's cluster barrier pulls the
+// two columns of its next pair from the CTAs that hold them, through
+// distributed shared memory: 2m doubles move per CTA and round.  At the end
+// of a sweep each CTA publishes whether it rotated and all CTAs stop on the
+// same OR.  Same round-robin pair order, rotations and stopping rule as
+// k_jacobi.
+constexpr int kJC = 256;
+constexpr int kJCW = kJC / 32;
+constexpr int kJacobiClusterMaxEll = 32;
+constexpr int kJacobiClusterMaxRows = 6144;   // 4 columns of m doubles per CTA: 192 KB
+
+// Pair pi of round r of the round-robin order on lp (even) players.
+__device__ __forceinline__ void rr_pair(int pi, int r, int lp, int& p, int& q) {
+  const int L = lp - 1;
+  if (pi == 0) { p = r; q = lp - 1; }
+  else { p = (r + pi) % L; q = (r - pi + L) % L; }
+  if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// Pair index that holds column j in round r.
+__device__ __forceinline__ int rr_holder(int j, int r, int lp) {
+  const int L = lp - 1;
+  if (j == lp - 1) return 0;
+  const int d = ((j - r) % L + L) % L;
+  if (d == 0) return 0;
+  return d <= (L - 1) / 2 ? d : L - d;
+}
+
+__global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* B, int ld, double tol,
+                                                        int max_sweeps, const int* err, int* sweeps_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  extern __shared__ double buf[];        // [2 buffers][2 slots][m], then C sweep flags
+  double* flags = buf + 4 * (size_t)m;
+  __shared__ double red[3 * kJCW];
+  __shared__ double rot[3];              // c, s, rotate?
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (*err) return;                      // every CTA reads the same word: all leave together
+  const int lp = ell + (ell & 1);
+  const int L = lp - 1;                  // rounds per sweep
+  auto col = [&](int b, int slot) { return buf + ((size_t)b * 2 + slot) * m; };
+  int cur = 0;
+  {
+    int p, q;
+    rr_pair(rank, 0, lp, p, q);
+    for (int i = tid; i < m; i += kJC) {
+      col(0, 0)[i] = B[(size_t)p * ld + i];
+      col(0, 1)[i] = q < ell ? B[(size_t)q * ld + i] : 0.0;
+    }
+  }
+  cl.sync();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double mine = 0.0;
+    for (int r = 0; r < L; ++r) {
+      int p, q;
+      rr_pair(rank, r, lp, p, q);
+      if (q < ell) {
+        double* bp = col(cur, 0);
+        double* bq = col(cur, 1);
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = tid; i < m; i += kJC) {
+          const double x = bp[i], y = bq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (lane == 0) { red[wid] = al; red[kJCW + wid] = be; red[2 * kJCW + wid] = ga; }
+        __syncthreads();
+        if (wid == 0) {
+          double a = lane < kJCW ? red[lane] : 0.0;
+          double b = lane < kJCW ? red[kJCW + lane] : 0.0;
+          double g = lane < kJCW ? red[2 * kJCW + lane] : 0.0;
+          a = warp_sum(a);
+          b = warp_sum(b);
+          g = warp_sum(g);
+          if (lane == 0) {
+            if (jacobi_needs_rotation(a, b, g, tol)) {
+              double c, sn;
+              jacobi_rotation(a, b, g, c, sn);
+              rot[0] = c; rot[1] = sn; rot[2] = 1.0;
+            } else {
+              rot[2] = 0.0;
+            }
+          }
+        }
+        __syncthreads();
+        if (rot[2] != 0.0) {
+          const double c = rot[0], sn = rot[1];
+          for (int i = tid; i < m; i += kJC) {
+            const double x = bp[i], y = bq[i];
+            bp[i] = c * x - sn * y;
+            bq[i] = sn * x + c * y;
+          }
+          mine = 1.0;
+        }
+      }
+      cl.sync();                         // every rotation of round r is done
+      // pull the two columns of the next round's pair from their holders
+      const int rn = (r + 1) % L;
+      int pn, qn;
+      rr_pair(rank, rn, lp, pn, qn);
+      const int nxt = cur ^ 1;
+      for (int s = 0; s < 2; ++s) {
+        const int j = s == 0 ? pn : qn;
+        double* dst = col(nxt, s);
+        if (j >= ell) {
+          for (int i = tid; i < m; i += kJC) dst[i] = 0.0;
+          continue;
+        }
+        const int h = rr_holder(j, r, lp);
+        int hp, hq;
+        rr_pair(h, r, lp, hp, hq);
+        const double* src = cl.map_shared_rank(col(cur, j == hp ? 0 : 1), h);
+        for (int i = tid; i < m; i += kJC) dst[i] = src[i];
+      }
+      cur = nxt;
+      __syncthreads();                   // rot[] and red[] are rewritten next round
+    }
+    if (tid < C) *cl.map_shared_rank(flags + rank, tid) = mine;
+    cl.sync();
+    double any = 0.0;
+    for (int k = 0; k < C; ++k) any += flags[k];
+    if (any == 0.0) break;
+  }
+  // the columns of round 0's pairs are current in every CTA: write them back
+  {
+    int p, q;
+    rr_pair(rank, 0, lp, p, q);
+    for (int i = tid; i < m; i += kJC) {
+      B[(size_t)p * ld + i] = col(cur, 0)[i];
+      if (q < ell) B[(size_t)q * ld + i] = col(cur, 1)[i];
+    }
+  }
+  if (rank == 0 && tid == 0) *sweeps_out = sweep < max_sweeps ? sweep + 1 : max_sweeps + 1;
+  cl.sync();                             // no CTA leaves while a peer may still read its columns
+}
+
 // G[j][j] += f * trace(G)  (one CTA): the shift of the first Cholesky-QR pass.
 __global__ void __launch_bounds__(kNT) k_shift_trace(int ell, double* G, double f) {
   __shared__ double sh[kWarps];
@@ -487,7 +636,10 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   double* Bsv = cw.Ynu;           // matrix whose column norms / directions give U and Sigma
   int jm = m, jld = ld;           // Jacobi problem: rows and leading dimension
   double* Jmat = cw.Ynu;
-  const bool direct = m <= 2 * ell && (long long)m * ell <= kJacobiSmemElems;
+  // direct on B when the cluster Jacobi takes it (ell <= 32, one CTA per
+  // pair), or when B is nearly square; otherwise through a QR of B
+  const bool direct = (ell <= kJacobiClusterMaxEll && ell >= 2 && m <= kJacobiClusterMaxRows) ||
+                      (m <= 2 * ell && (long long)m * ell <= kJacobiSmemElems);
   if (!direct) {
     // B = Q R by a shifted three-pass Cholesky QR (the first pass
     // shifted by 1e-10 trace(B^T B) so it cannot break down), then the SVD of
@@ -519,7 +671,33 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   }
   double tol = sqrt((double)jm) * 0x1.0p-53;
   if (tol < 0x1.0p-52) tol = 0x1.0p-52;
-  if ((long long)jm * ell <= kJacobiSmemElems) {
+  if (ell <= kJacobiClusterMaxEll && ell >= 2 && jm <= kJacobiClusterMaxRows) {
+    // one CTA per column pair of a round, in one thread-block cluster
+    const int C = (ell + 1) / 2;
+    const size_t sm = sizeof(double) * (4 * (size_t)jm + C);
+    e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (4 * (size_t)kJacobiClusterMaxRows + 16)));
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+      e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kJC);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launches(1);
+    e = cudaLaunchKernelEx(&cfg, k_jacobi_cluster, jm, ell, Jmat, jld, tol, (int)CoreWork::kMaxSweeps,
+                           (const int*)err, si + SI_SWEEPS);
+  } else if ((long long)jm * ell <= kJacobiSmemElems) {
     // one-sided Jacobi in one CTA's shared memory
     const size_t sm = sizeof(double) * (size_t)jm * ell;
     // the attribute is set to the kernel's maximum, never lowered: handles on

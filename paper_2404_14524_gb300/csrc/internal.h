@@ -205,12 +205,14 @@ struct ClusterPcgTask {
   int* err;                             // device error word
 };
 struct ClusterPlan {
-  int C = 0;                            // CTAs per cluster (8 or 16)
+  int C = 0;                            // CTAs per cluster (4, 8 or 16)
   int a_smem = 0;                       // A's column band held in shared memory
   size_t smem_bytes = 0;                // dynamic shared memory per CTA
 };
-// Plan for an m x n system with rank ell; false when no cluster fits.
-bool pcg_cluster_plan(int m, int n, int ell, ClusterPlan* plan);
+// Plan for an m x n system with rank ell: policy 0 for the latency of one
+// solve, 1 for many solves side by side, 2 the latency plan if one exists,
+// else the throughput plan; false when no cluster fits.
+bool pcg_cluster_plan(int m, int n, int ell, int policy, ClusterPlan* plan);
 // One system (`task`, tasks == nullptr) or `count` systems from the device
 // array `tasks`, each planned no larger than `plan`.
 cudaError_t pcg_cluster_f64(cudaStream_t st, const ClusterPlan& plan, const ClusterPcgTask& task,

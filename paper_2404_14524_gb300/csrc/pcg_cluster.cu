@@ -419,15 +419,24 @@ bool launchable(int C, size_t smem_bytes, bool a_smem) {
 
 }  // namespace
 
-bool pcg_cluster_plan(int m, int n, int ell, ClusterPlan* plan) {
+bool pcg_cluster_plan(int m, int n, int ell, int policy, ClusterPlan* plan) {
   if (m <= 0 || n <= 0 || ell <= 0) return false;
-  for (int C : {kMaxC, 8}) {
-    for (int as = 1; as >= 0; --as) {
+  // latency (one system at a time): 16 or 8 SMs with A on chip; a larger A
+  // is faster on the cooperative grid.  Throughput (many systems side by
+  // side): 8 or 4 SMs per system, A on chip or read from L2, since the FP64
+  // work of an SM is used best by small clusters.
+  struct Cand { int C, as; };
+  static const Cand lat[] = {{kMaxC, 1}, {8, 1}};
+  static const Cand thr[] = {{8, 1}, {4, 1}, {8, 0}, {4, 0}};
+  const Cand* lists[2] = {lat, thr};
+  const int lens[2] = {2, 4};
+  for (int li = 0; li < 2; ++li) {
+    if ((li == 0 && policy == 1) || (li == 1 && policy == 0)) continue;
+    for (int k = 0; k < lens[li]; ++k) {
+      const int C = lists[li][k].C, as = lists[li][k].as;
       const Layout L = make_layout(m, n, ell, C, as != 0);
       const size_t bytes = L.total * sizeof(double);
       if (bytes > kSmemCap) continue;
-      // A streamed from L2 by C SMs only pays while the matrix is small
-      if (!as && (long long)m * n > (1ll << 20)) continue;
       if (!launchable(C, bytes, as != 0)) continue;
       plan->C = C;
       plan->a_smem = as;

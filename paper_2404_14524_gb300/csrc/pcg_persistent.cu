@@ -11,6 +11,7 @@
 // barriers per iteration:
 //
 //   1. p = z + beta p (smem, all rows);  t = D .* (A^T p) over own columns
+//      (warps split the rows, lanes the columns, a tree over the warps)
 //   -- barrier (t complete)
 //   2. w = A t + delta p over own rows; partial p^T w            -> alpha
 //   3. x += alpha p; r -= alpha w over own rows; partials U^T r, r^T r
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
   __shared__ double sh[kPW * 4 + 2];
   __shared__ double ws[kMaxEll];            // (lam_ell + delta) / (lam + delta) - 1
   __shared__ double ss[kMaxEll];            // s = U^T r
+  __shared__ double red[kPW * 64];          // per-warp partials of A^T p
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int rb = (m + gridDim.x - 1) / gridDim.x;
@@ -135,17 +137,45 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
     // 1. p = z + beta p in shared memory (every CTA, all rows); t over own columns
     for (int i = tid; i < m; i += kPT) ps[i] = fma(beta, it == 0 ? 0.0 : ps[i], __ldcg(S.z + i));
     __syncthreads();
-    for (int j = j0 + tid; j < j1; j += kPT) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int i = 0;
-      for (; i + 4 <= m; i += 4) {
-        a0 = fma(__ldg(A + (long long)(i + 0) * lda + j), ps[i + 0], a0);
-        a1 = fma(__ldg(A + (long long)(i + 1) * lda + j), ps[i + 1], a1);
-        a2 = fma(__ldg(A + (long long)(i + 2) * lda + j), ps[i + 2], a2);
-        a3 = fma(__ldg(A + (long long)(i + 3) * lda + j), ps[i + 3], a3);
+    // warps over rows (two interleaved accumulators each), lanes over 64
+    // columns, then a fixed tree over the warps: no thread walks a whole
+    // column, so the FP64 latency chains stay short
+    for (int c0 = j0; c0 < j1; c0 += 64) {
+      double a[2] = {0.0, 0.0}, b[2] = {0.0, 0.0};
+      int i = wid;
+      for (; i + kPW < m; i += 2 * kPW) {
+        const double p0 = ps[i], p1 = ps[i + kPW];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = c0 + u * 32 + lane;
+          if (j < j1) {
+            a[u] = fma(__ldg(A + (long long)i * lda + j), p0, a[u]);
+            b[u] = fma(__ldg(A + (long long)(i + kPW) * lda + j), p1, b[u]);
+          }
+        }
       }
-      for (; i < m; ++i) a0 = fma(__ldg(A + (long long)i * lda + j), ps[i], a0);
-      __stcg(S.t + j, D[j] * ((a0 + a1) + (a2 + a3)));
+      if (i < m) {
+        const double p0 = ps[i];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = c0 + u * 32 + lane;
+          if (j < j1) a[u] = fma(__ldg(A + (long long)i * lda + j), p0, a[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) red[wid * 64 + u * 32 + lane] = a[u] + b[u];
+      __syncthreads();
+      if (tid < 64 && c0 + tid < j1) {
+        double w8[kPW];
+#pragma unroll
+        for (int w = 0; w < kPW; ++w) w8[w] = red[w * 64 + tid];
+#pragma unroll
+        for (int st = 1; st < kPW; st <<= 1)
+#pragma unroll
+          for (int w = 0; w + st < kPW; w += 2 * st) w8[w] += w8[w + st];
+        __stcg(S.t + c0 + tid, D[c0 + tid] * w8[0]);
+      }
+      __syncthreads();
     }
     __threadfence();
     if (!grid_barrier(bar, err)) return;
@@ -157,9 +187,16 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
     double v = 0.0;
     for (int i = i0 + wid; i < i1; i += kPW) {
       const double* a = A + (long long)i * lda;
-      double acc = 0.0;
-      for (int j = lane; j < n; j += 32) acc = fma(__ldg(a + j), ts[j], acc);
-      acc = warp_sum(acc);
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = lane;
+      for (; j + 96 < n; j += 128) {
+        a0 = fma(__ldg(a + j), ts[j], a0);
+        a1 = fma(__ldg(a + j + 32), ts[j + 32], a1);
+        a2 = fma(__ldg(a + j + 64), ts[j + 64], a2);
+        a3 = fma(__ldg(a + j + 96), ts[j + 96], a3);
+      }
+      for (; j < n; j += 32) a0 = fma(__ldg(a + j), ts[j], a0);
+      const double acc = warp_sum((a0 + a1) + (a2 + a3));
       if (lane == 0) {
         const double wi = fma(delta, ps[i], acc);
         __stcg(S.w + i, wi);
@@ -225,9 +262,9 @@ cudaError_t pcg_persistent_f64(cudaStream_t st, int m, int n, const double* A, l
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kPT, dsm);
   if (e != cudaSuccess) return e;
-  // about 64K multiply-adds of the operator per CTA (the FP64 rate of an SM
+  // about 16K multiply-adds of the operator per CTA (the FP64 rate of an SM
   // bounds each phase), at least 2 CTAs, at most one CTA per SM
-  long long g = ((long long)m * n + 65535) / 65536;
+  long long g = ((long long)m * n + 16383) / 16384;
   if (g < 2) g = 2;
   if (g > num_sms) g = num_sms;
   if (g > (long long)per_sm * num_sms) g = (long long)per_sm * num_sms;

@@ -77,6 +77,7 @@ struct nys_solver {
   // FP64 PCG route: 0 by size (cluster, else cooperative, else graph),
   // 1 cluster only, 2 cooperative only, 3 graph only (NYS_PCG_PATH)
   int pcg_path = 0;
+  int plan_policy = 0;         // cluster plans: 0 latency, 2 latency else throughput (NYS_PCG_PATH=cluster)
   int cp_m = -1, cp_n = -1, cp_ell = -1;   // key of the cached cluster plan
   bool cp_ok = false;
   ClusterPlan cp;
@@ -345,11 +346,13 @@ bool ensure_pcg_graph(nys_solver* h, int m, int n, const OpSpec& op, int ell, co
 }
 
 // Route of an FP64 PCG solve (NYS_ROUTE_*): a thread-block cluster when a
-// cluster plan exists, else one cooperative launch when it fits, else the
-// graph of per-step kernels; NYS_PCG_PATH restricts the choice.
+// cluster plan exists (A on chip; for a batch worker also A in L2), else one
+// cooperative launch when it fits, else the graph of per-step kernels;
+// NYS_PCG_PATH restricts the choice (the cluster route then falls back to a
+// throughput plan, so that it can be tested on L2-resident A).
 int fp64_route(nys_solver* h, int m, int n, int ell) {
   if (h->cp_m != m || h->cp_n != n || h->cp_ell != ell) {
-    h->cp_ok = pcg_cluster_plan(m, n, ell, &h->cp);
+    h->cp_ok = pcg_cluster_plan(m, n, ell, h->plan_policy, &h->cp);
     h->cp_m = m; h->cp_n = n; h->cp_ell = ell;
   }
   if ((h->pcg_path == 0 || h->pcg_path == 1) && h->cp_ok)
@@ -699,6 +702,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   if (const char* env = std::getenv("NYS_PCG_PATH")) {
     const std::string v(env);
     h->pcg_path = v == "cluster" ? 1 : v == "cooperative" ? 2 : v == "graph" ? 3 : 0;
+    if (h->pcg_path == 1) h->plan_policy = 2;
   }
   if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
@@ -867,6 +871,14 @@ int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result*
     h->workers.push_back(w);
     h->worker_streams.push_back(s);
   }
+  // largest problems first (longest-processing-time order keeps the tail
+  // short); every launch shape depends on the problem alone, so a batched
+  // solve gives the same bits as a sequential one
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)p[a].m * p[a].n > (long long)p[b].m * p[b].n;
+  });
   std::atomic<int> next{0};
   std::vector<std::thread> pool;
   pool.reserve(want);
@@ -874,7 +886,7 @@ int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result*
     pool.emplace_back([&, t]() {
       cudaSetDevice(h->device);
       nys_solver* w = h->workers[t];
-      for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) nys_solve(w, &p[i], &r[i]);
+      for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) nys_solve(w, &p[order[k]], &r[order[k]]);
     });
   }
   for (auto& th : pool) th.join();
@@ -1161,9 +1173,9 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
       const double t_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
       std::fprintf(stderr,
                    "[nys] k=%d mu=%.3e rel_p=%.3e rel_d=%.3e rho=%.2e delta=%.2e ap=%.3f ad=%.3f pcg=%d "
-                   "refine=%d sketch+core=%.1fms iter=%.1fms\n",
+                   "refine=%d sketch+core=%.1fms jacobi_sweeps=%d iter=%.1fms\n",
                    k, mu, rel_p, rel_d, rho, delta, ap, ad, r->pcg_iters_total - pcg_before,
-                   r->refine_steps - ref_before, 1e3 * t_pre, 1e3 * t_it);
+                   r->refine_steps - ref_before, 1e3 * t_pre, h->h_si[SI_SWEEPS], 1e3 * t_it);
     }
     mu_prev = mu;
     ++k;

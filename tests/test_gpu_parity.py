@@ -120,13 +120,14 @@ def _factor_pair(nys, m, n, ell, seed, rank=None, dscale=1.0):
     return h, A, D, Om, Fw, U.cpu().numpy().T, lam.cpu().numpy(), nu
 
 
-@pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (301, 450, 47), (64, 64, 64), (5, 9, 1),
-                                     (1024, 1500, 32), (600, 900, 120), (1000, 1500, 201)])
+@pytest.mark.parametrize("m,n,ell", [(200, 500, 20), (301, 450, 47), (64, 64, 64), (5, 9, 1), (7, 12, 7),
+                                     (1024, 1500, 32), (6200, 6300, 20), (600, 900, 120), (1000, 1500, 201)])
 def test_nystrom_factor_matches_oracle(nys, m, n, ell):
-    """ell <= 96 with m ell <= 25600: one-sided Jacobi on B in one CTA's
-    shared memory; otherwise QR of B first (shifted Cholesky QR3) and Jacobi
-    on the ell x ell factor (in shared memory up to ell = 160, else the
-    cooperative kernel)."""
+    """2 <= ell <= 32 and m <= 6144: one-sided Jacobi on B by a thread-block
+    cluster (one CTA per column pair); B nearly square and small: Jacobi on
+    B in one CTA's shared memory; otherwise QR of B first (shifted Cholesky
+    QR3) and Jacobi on the ell x ell factor (cluster for ell <= 32, one CTA
+    up to ell = 160, else the cooperative kernel)."""
     h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, m, n, ell, seed=m + ell)
     assert nu == Fw.nu
     assert np.all(np.diff(lam) <= 0) and np.all(lam >= 0)
@@ -402,5 +403,7 @@ def test_one_launch_pcg_routes_match_the_graph_pcg(nys, monkeypatch, m, n, ell, 
     for forced in (5, -1):
         a, ia, ra, _ = nys.nys_pcg(hr, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
         b, ib, rb, _ = nys.nys_pcg(h0, T(A), T(D), 1e-4, P(U), T(lam), T(xi), 1e-9, 500, forced=forced)
-        assert abs(ia - ib) <= (0 if forced >= 0 else 1)
+        # at the tolerance crossing the count moves with the summation order
+        # (as for the oracle comparison above): within max(2, 5%)
+        assert abs(ia - ib) <= (0 if forced >= 0 else max(2, int(0.05 * ib)))
         assert relerr(a, b.cpu().numpy()) <= (1e-11 if forced >= 0 else 1e-7)
