@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <condition_variable>
 #include <vector>
 
 #include <atomic>
@@ -65,6 +66,11 @@ struct nys_solver {
   cudaStream_t cap_stream = nullptr;
   // device time of the PCG solves: events around each solve on the stream
   cudaEvent_t ev_pcg0 = nullptr, ev_pcg1 = nullptr;
+  // lock-step batches: a worker's prepared request; the shared launch (master)
+  cudaEvent_t ev_req = nullptr, ev_b0 = nullptr, ev_b1 = nullptr;
+  ClusterPcgTask* d_tasks = nullptr;   // device task array of the shared launch
+  ClusterPcgTask* h_tasks = nullptr;   // pinned staging of the same
+  int task_cap = 0;
   double pcg_ms = 0.0;
   cudaGraph_t pcg_graph = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
@@ -454,18 +460,34 @@ int run_pcg(nys_solver* h, int m, int n, const double* A, long long lda, const d
   return run_pcg(h, m, n, op, delta, ell, U, ld, lamh, xi, out, eta, max_iter, forced, iters);
 }
 
+// Algorithm 4, first half: xi = r_p + A D (r_d - X^{-1} r_xz) into h->xi.
+int newton_begin(nys_solver* h, int m, int n, const double* A, long long lda, const double* x,
+                 const double* D, const double* r_d, const double* r_p, const double* r_xz) {
+  CK(newton_rhs_f64(h->st, n, D, r_d, r_xz, x, h->t_n));
+  CK(gemv_n_f64(h->st, m, n, A, lda, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi));
+  return NYS_OK;
+}
+
+// Algorithm 4, second half: dx = D (A^T dy - r_d + X^{-1} r_xz), dz = X^{-1} (r_xz - Z dx).
+int newton_end(nys_solver* h, int m, int n, const double* A, long long lda, const double* x,
+               const double* z, const double* D, const double* r_d, const double* r_xz, const double* dy,
+               double* dx, double* dz) {
+  CK(gemv_t_f64(h->st, m, n, A, lda, dy, nullptr, h->g_n, h->split_buf, h->split_cap));
+  CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
+  return NYS_OK;
+}
+
 // Algorithm 4: Newton direction through the normal equations.
 int newton(nys_solver* h, int m, int n, const double* A, long long lda, const double* x,
            const double* z, const double* D, double delta, const double* r_d, const double* r_p,
            const double* r_xz, int ell, const double* U, int ld, const double* lamh, double eta,
            int max_iter, int forced, double* dx, double* dy, double* dz, int* iters) {
-  CK(newton_rhs_f64(h->st, n, D, r_d, r_xz, x, h->t_n));
-  CK(gemv_n_f64(h->st, m, n, A, lda, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi));
-  int rc = run_pcg(h, m, n, A, lda, D, delta, ell, U, ld, lamh, h->xi, dy, eta, max_iter, forced, iters);
+  int rc = newton_begin(h, m, n, A, lda, x, D, r_d, r_p, r_xz);
+  if (rc != NYS_OK) return rc;
+  rc = run_pcg(h, m, n, A, lda, D, delta, ell, U, ld, lamh, h->xi, dy, eta, max_iter, forced, iters);
   if (rc < 0) return rc;
-  CK(gemv_t_f64(h->st, m, n, A, lda, dy, nullptr, h->g_n, h->split_buf, h->split_cap));
-  CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
-  return rc;
+  const int rc2 = newton_end(h, m, n, A, lda, x, z, D, r_d, r_xz, dy, dx, dz);
+  return rc2 != NYS_OK ? rc2 : rc;
 }
 
 // ---------------------------------------------------------------- precision form
@@ -623,6 +645,465 @@ int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, co
 
 }  // namespace
 
+// One IP-PMM solve (Algorithm 6 with the Algorithm 5 predictor-corrector) as
+// a resumable sequence of phases, so that a driver can stop it where a
+// Newton system's PCG solve is due: nys_solve runs one to the end, calling
+// run_pcg for each request; nys_solve_batched advances many in lock step and
+// serves the requests of all of them with one launch.
+struct PcgRequest {
+  bool active = false;
+  const double *A = nullptr, *D = nullptr, *xi = nullptr;
+  long long lda = 0;
+  double* out = nullptr;
+  double delta = 0.0, eta = 0.0;
+  int max_iter = 0, forced = -1;
+  int rc = NYS_OK, iters = 0;       // filled in by whoever serves the request
+};
+
+struct IpmRun {
+  nys_solver* h = nullptr;
+  const nys_problem* p = nullptr;
+  nys_result* r = nullptr;
+  std::chrono::steady_clock::time_point t0, tk0;
+  int m = 0, n = 0, lp = 0, ell = 0;
+  long long lda = 0;
+  Prob P{};
+  const double* A = nullptr;
+  const double *b = nullptr, *c = nullptr, *q = nullptr;
+  double bnorm = 0.0, cnorm = 0.0, rho = 0.0, delta = 0.0, mu = 0.0, mu_prev = 0.0;
+  double rel_p = 0.0, rel_d = 0.0, eta = 0.0, t_pre = 0.0;
+  int forced_idx = 0, warn = NYS_OK, k = 0, status = NYS_WARN_MAXITER;
+  int pcg_before = 0, ref_before = 0;
+  bool done = false;
+  PcgRequest req;
+
+  int next_forced() {
+    const nys_options& o = h->opt;
+    if (o.forced_pcg_iters && forced_idx < o.n_forced_pcg) return o.forced_pcg_iters[forced_idx++];
+    return -1;
+  }
+  void log_pcg(int it) {
+    r->pcg_iters_total += it;
+    if (r->pcg_log && r->pcg_log_len < r->pcg_log_cap) r->pcg_log[r->pcg_log_len++] = it;
+  }
+  // a phase ends the solve with `code`
+  void stop(int code) {
+    status = code;
+    done = true;
+    req.active = false;
+  }
+  void request(double* out) {
+    req.active = true;
+    req.A = A; req.lda = lda; req.D = h->D; req.xi = h->xi; req.out = out;
+    req.delta = delta; req.eta = eta; req.max_iter = h->opt.max_pcg_iter; req.forced = next_forced();
+    req.rc = NYS_OK; req.iters = 0;
+  }
+  // the request's outcome: count it, keep a warning, stop on an error
+  bool take_request() {
+    req.active = false;
+    if (req.rc < 0) { stop(req.rc); return false; }
+    if (req.rc > 0) warn = req.rc;
+    log_pcg(req.iters);
+    return true;
+  }
+  int start(nys_solver* h_, const nys_problem* p_, nys_result* r_);
+  int top();
+  int mid();
+  int bottom();
+  int finish();
+};
+
+int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
+  h = h_; p = p_; r = r_;
+  t0 = std::chrono::steady_clock::now();
+  if (!p || !r) { done = true; return status = fail(h, NYS_ERR_ARG, "nys_solve: null problem or result"); }
+  m = p->m; n = p->n;
+  const nys_options& o = h->opt;
+  lp = o.precision_mode == 1;
+  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n ||
+      p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 ||
+      !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0 || p->ell < 0) {
+    done = true;
+    return status = fail(h, NYS_ERR_ARG,
+                         "nys_solve: bad problem (sizes, dtype for the precision mode, or null pointers)");
+  }
+  ell = std::min(std::min(h->ell_cap, m), p->ell > 0 ? p->ell : h->ell_cap);
+  lda = p->lda;
+  r->status = NYS_OK;
+  r->ipm_iters = 0;
+  r->pcg_iters_total = 0;
+  r->refine_steps = 0;
+  r->pcg_log_len = 0;
+  r->pcg_seconds = 0.0;
+  h->pcg_ms = 0.0;
+  done = true;                 // until the setup below succeeds
+  status = NYS_ERR_CUDA;
+
+  // Problem data on the device (staged when the caller passes host memory).
+  const size_t esz = lp ? sizeof(float) : sizeof(double);
+  const void* Av = p->A;
+  b = p->b; c = p->c; q = p->q;
+  if (p->host) {
+    const size_t a_bytes = align_up((size_t)m * lda * esz, 256);
+    const size_t need = a_bytes + 3 * align_up(sizeof(double) * (size_t)n, 256) +
+                        align_up(sizeof(double) * (size_t)m, 256);
+    if (need > h->stage_bytes) {
+      if (h->stage) cudaFree(h->stage);
+      h->stage = nullptr;
+      h->stage_bytes = 0;
+      if (cudaMalloc(&h->stage, need) != cudaSuccess) {
+        cudaGetLastError();
+        return status = fail(h, NYS_ERR_NOMEM, "nys_solve: cannot stage a host problem of %zu bytes", need);
+      }
+      h->stage_bytes = need;
+    }
+    char* s = static_cast<char*>(h->stage);
+    void* dA = s;
+    double* db = reinterpret_cast<double*>(s + a_bytes);
+    double* dc = reinterpret_cast<double*>(s + a_bytes + align_up(sizeof(double) * m, 256));
+    double* dq = reinterpret_cast<double*>(reinterpret_cast<char*>(dc) + align_up(sizeof(double) * n, 256));
+    CK(cudaMemcpyAsync(dA, p->A, (size_t)m * lda * esz, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(db, p->b, sizeof(double) * m, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(dc, p->c, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(dq, p->q, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
+    Av = dA; b = db; c = dc; q = dq;
+  }
+  P = Prob{m, n, lp, lp ? nullptr : static_cast<const double*>(Av), lp ? static_cast<const float*>(Av) : nullptr, lda};
+  A = P.A64;
+  h->lp_bf16_stage = true;
+  if (lp)   // BF16 A and A^T for the inner solves and the sketch, FP32 A^T for residuals
+    CK(convert_transpose(h->st, m, n, 0, Av, lda, h->Ab, h->ld_b, h->AbT, h->ld_bt, h->AfT, h->ld_ft));
+  const cudaMemcpyKind kin = p->host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->x, p->x0, sizeof(double) * n, kin, h->st));
+  CK(cudaMemcpyAsync(h->y, p->y0, sizeof(double) * m, kin, h->st));
+  CK(cudaMemcpyAsync(h->z, p->z0, sizeof(double) * n, kin, h->st));
+  if (p->lam0) CK(cudaMemcpyAsync(h->lam, p->lam0, sizeof(double) * m, kin, h->st));
+  else CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  if (p->zeta0) CK(cudaMemcpyAsync(h->zeta, p->zeta0, sizeof(double) * n, kin, h->st));
+  else CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
+  CK(dot_f64(h->st, m, b, b, h->red_out + 8, h->red));
+  CK(dot_f64(h->st, n, c, c, h->red_out + 9, h->red));
+  int rc = sync_scalars(h, 10);
+  if (rc != NYS_OK) return r->status = status = rc;
+  bnorm = std::sqrt(h->h_red[8]);
+  cnorm = std::sqrt(h->h_red[9]);
+  rho = o.rho0;
+  delta = o.delta0;
+  status = NYS_WARN_MAXITER;
+  done = false;
+  return NYS_OK;
+}
+
+// Top of an iteration: residuals, termination, PEU, scaling, sketch and core,
+// then the predictor's Newton system (a PCG request, or solved in place by the
+// precision form).
+int IpmRun::top() {
+  const nys_options& o = h->opt;
+  int rc = op_Ax(h, P, h->x, 0.0, nullptr, h->Ax);
+  if (rc == NYS_OK) rc = op_Aty(h, P, h->y, nullptr, h->Aty);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
+                       rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
+  rc = sync_scalars(h, 3);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  const double nrd = std::sqrt(h->h_red[0]), nrp = std::sqrt(h->h_red[2]);
+  mu = h->h_red[1] / n;
+  if (!std::isfinite(nrd) || !std::isfinite(nrp) || !std::isfinite(mu)) {
+    stop(fail(h, NYS_ERR_NUMERIC, "non-finite residual at IPM iteration %d", k));
+    return status;
+  }
+  rel_p = nrp / (1.0 + bnorm);
+  rel_d = nrd / (1.0 + cnorm);
+  if (k > 0) {
+    // PMM parameter update (reading of PEU): re-centre the proximal
+    // estimates on the iterate and decay rho, delta with the change of mu.
+    const double den = std::max(mu_prev, mu);
+    const double r_mu = den > 0.0 ? std::fabs(mu - mu_prev) / den : 0.0;
+    CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    delta = std::max(o.reg_floor, (1.0 - r_mu) * delta);
+    rho = std::max(o.reg_floor, (1.0 - r_mu) * rho);
+    // predictor right-hand sides with the updated PMM parameters
+    CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
+                         rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
+  }
+  // Termination (reading of TC: relative infeasibilities and mu).
+  if (o.forced_ipm_iters >= 0) {
+    if (k >= o.forced_ipm_iters) {
+      stop((rel_p <= o.tol && rel_d <= o.tol && mu <= o.tol) ? NYS_OK : NYS_WARN_MAXITER);
+      return NYS_OK;
+    }
+  } else if (rel_p <= o.tol && rel_d <= o.tol && mu <= o.tol) {
+    stop(NYS_OK);
+    return NYS_OK;
+  }
+  if (k >= o.max_ipm_iter) { stop(NYS_WARN_MAXITER); return NYS_OK; }
+
+  // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).
+  tk0 = std::chrono::steady_clock::now();
+  CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
+  rc = op_sketch(h, P, p->k0 + k, ell, h->D);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
+                      h->cw, h->num_sms));
+  eta = std::max(1e-10, std::min(1e-2, 0.1 * mu));
+  t_pre = 0.0;
+  if (h->trace) {
+    cudaStreamSynchronize(h->st);
+    t_pre = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
+  }
+  pcg_before = r->pcg_iters_total;
+  ref_before = r->refine_steps;
+
+  // Predictor (Algorithm 5, first step).
+  if (lp) {
+    int it = 0, ref = 0;
+    rc = newton_lp(h, P, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, eta, o.max_pcg_iter,
+                   h->dxp, h->dyp, h->dzp, &it, &ref);
+    r->refine_steps += ref;
+    req.rc = rc;
+    req.iters = it;
+    req.active = false;
+    return NYS_OK;
+  }
+  rc = newton_begin(h, m, n, A, lda, h->x, h->D, h->r_d, h->r_p, h->r_xz);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  request(h->dyp);
+  return NYS_OK;
+}
+
+// After the predictor's PCG: its direction, step lengths, mu_aff, and the
+// corrector's Newton system.
+int IpmRun::mid() {
+  const nys_options& o = h->opt;
+  if (!take_request()) return status;
+  if (!lp) {
+    const int rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, h->r_d, h->r_xz, h->dyp, h->dxp, h->dzp);
+    if (rc != NYS_OK) { stop(rc); return rc; }
+  }
+  CK(step_ratios_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, h->red_out, h->red));
+  int rc = sync_scalars(h, 2);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  const double ap_bar = 0.995 * std::min(1.0, h->h_red[0]);
+  const double ad_bar = 0.995 * std::min(1.0, h->h_red[1]);
+  CK(mu_aff_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, ap_bar, ad_bar, h->red_out, h->red));
+  rc = sync_scalars(h, 1);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  const double mu_aff = h->h_red[0] / n;
+  const double mu_t = mu_aff * mu_aff * mu_aff / (mu * mu);
+
+  // Corrector (Eq. corrector-RHS): r_d = r_p = 0, r_xz = mu_t - dxp dzp.
+  CK(corrector_rhs_f64(h->st, n, mu_t, h->dxp, h->dzp, h->r_xz));
+  if (lp) {
+    int it = 0, ref = 0;
+    rc = newton_lp(h, P, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, eta, o.max_pcg_iter,
+                   h->dxc, h->dyc, h->dzc, &it, &ref);
+    r->refine_steps += ref;
+    req.rc = rc;
+    req.iters = it;
+    req.active = false;
+    return NYS_OK;
+  }
+  rc = newton_begin(h, m, n, A, lda, h->x, h->D, nullptr, nullptr, h->r_xz);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  request(h->dyc);
+  return NYS_OK;
+}
+
+// After the corrector's PCG: the combined direction and the step.
+int IpmRun::bottom() {
+  if (!take_request()) return status;
+  if (!lp) {
+    const int rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, nullptr, h->r_xz, h->dyc, h->dxc, h->dzc);
+    if (rc != NYS_OK) { stop(rc); return rc; }
+  }
+  CK(add_dirs_f64(h->st, m, n, h->dxp, h->dyp, h->dzp, h->dxc, h->dyc, h->dzc));
+  CK(step_ratios_f64(h->st, n, h->x, h->dxc, h->z, h->dzc, h->red_out, h->red));
+  const int rc = sync_scalars(h, 2);
+  if (rc != NYS_OK) { stop(rc); return rc; }
+  const double ap = 0.995 * std::min(1.0, h->h_red[0]);
+  const double ad = 0.995 * std::min(1.0, h->h_red[1]);
+  CK(ipm_update_f64(h->st, m, n, ap, ad, h->dxc, h->dyc, h->dzc, h->x, h->y, h->z));
+  if (h->trace) {
+    cudaStreamSynchronize(h->st);
+    const double t_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
+    std::fprintf(stderr,
+                 "[nys] k=%d mu=%.3e rel_p=%.3e rel_d=%.3e rho=%.2e delta=%.2e ap=%.3f ad=%.3f pcg=%d "
+                 "refine=%d sketch+core=%.1fms jacobi_sweeps=%d iter=%.1fms\n",
+                 k, mu, rel_p, rel_d, rho, delta, ap, ad, r->pcg_iters_total - pcg_before,
+                 r->refine_steps - ref_before, 1e3 * t_pre, h->h_si[SI_SWEEPS], 1e3 * t_it);
+  }
+  mu_prev = mu;
+  ++k;
+  return NYS_OK;
+}
+
+// Outputs and final measures.
+int IpmRun::finish() {
+  const cudaMemcpyKind kout = p->host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(r->x, h->x, sizeof(double) * n, kout, h->st));
+  CK(cudaMemcpyAsync(r->y, h->y, sizeof(double) * m, kout, h->st));
+  CK(cudaMemcpyAsync(r->z, h->z, sizeof(double) * n, kout, h->st));
+  if (r->lam) CK(cudaMemcpyAsync(r->lam, h->lam, sizeof(double) * m, kout, h->st));
+  if (r->zeta) CK(cudaMemcpyAsync(r->zeta, h->zeta, sizeof(double) * n, kout, h->st));
+  CK(objective_terms_f64(h->st, m, n, q, c, b, h->x, h->y, h->z, h->red_out + 4, h->red));
+  int rc2 = sync_scalars(h, 8);
+  const double xqx = h->h_red[4], cx = h->h_red[5], by = h->h_red[6];
+  const double pobj = 0.5 * xqx + cx, dobj = by - 0.5 * xqx;
+  r->ipm_iters = k;
+  r->rel_primal = rel_p;
+  r->rel_dual = rel_d;
+  r->mu = mu;
+  r->rel_gap = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj));
+  r->rho = rho;
+  r->delta = delta;
+  if (status == NYS_OK && warn != NYS_OK) status = warn;
+  if (status >= 0 && rc2 != NYS_OK) status = rc2;
+  if (status >= 0 && h->h_red[7] != 0.0) status = fail(h, NYS_ERR_NUMERIC, "non-finite final iterate");
+  r->status = status;
+  r->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r->pcg_seconds = h->pcg_ms * 1e-3;
+  return status;
+}
+
+// Serve one run's PCG request on its own handle (any route).
+void serve_single(IpmRun& run) {
+  PcgRequest& q = run.req;
+  nys_solver* h = run.h;
+  q.rc = run_pcg(h, run.m, run.n, q.A, q.lda, q.D, q.delta, run.ell, h->U, h->ld, h->lamh, q.xi, q.out,
+                 q.eta, q.max_iter, q.forced, &q.iters);
+}
+
+// ---------------------------------------------------------------- lock-step batches
+// nys_solve_batched advances up to max_batch solves side by side, one host
+// thread per solve, and meets at every Newton system: the thread that
+// arrives last launches the PCG solves of all systems that have a cluster
+// plan as one k_pcg_cluster launch over a task array (one cluster per
+// system; clusters beyond what fits run as earlier ones finish), on the
+// master handle's stream, ordered after each worker's preparation and before
+// its continuation by events.  Systems without a cluster plan are solved by
+// their own worker on the usual route.
+struct BatchSlot {
+  ClusterPlan plan;
+  bool has_plan = false;
+  bool batched = false;        // the pending request is in the current shared launch
+  int acct_iters = -1;         // iterations of the previous shared launch, for its time share
+};
+
+struct Rendezvous {            // reusable barrier; the last thread to arrive runs `work` first
+  std::mutex mu;
+  std::condition_variable cv;
+  int n = 0, waiting = 0;
+  unsigned gen = 0;
+  template <class F> void arrive(F&& work) {
+    std::unique_lock<std::mutex> lk(mu);
+    const unsigned g = gen;
+    if (++waiting == n) {
+      work();
+      waiting = 0;
+      ++gen;
+      cv.notify_all();
+    } else {
+      cv.wait(lk, [&] { return gen != g; });
+    }
+  }
+};
+
+// Charge the previous shared launch's device time to its solves in proportion
+// to their iterations, then launch the pending requests that have a plan.
+int serve_batch(nys_solver* master, std::vector<IpmRun>& runs, std::vector<BatchSlot>& slots, bool& launched) {
+  nys_solver* h = master;
+  if (launched) {
+    long long tot = 0;
+    for (auto& sl : slots) if (sl.acct_iters > 0) tot += sl.acct_iters;
+    float ms = 0.f;
+    if (cudaEventSynchronize(master->ev_b1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, master->ev_b0, master->ev_b1) == cudaSuccess && tot > 0) {
+      for (size_t i = 0; i < runs.size(); ++i)
+        if (slots[i].acct_iters > 0) runs[i].h->pcg_ms += ms * (double)slots[i].acct_iters / (double)tot;
+    } else {
+      cudaGetLastError();
+    }
+    for (auto& sl : slots) sl.acct_iters = -1;
+    launched = false;
+  }
+  // group the planned requests by launch shape (cluster size, A on chip or not)
+  std::vector<int> idx;
+  for (size_t i = 0; i < runs.size(); ++i) {
+    slots[i].batched = false;
+    if (!runs[i].done && runs[i].req.active && slots[i].has_plan) idx.push_back((int)i);
+  }
+  if (idx.empty()) return NYS_OK;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    const ClusterPlan &pa = slots[a].plan, &pb = slots[b].plan;
+    return pa.C != pb.C ? pa.C > pb.C : pa.a_smem > pb.a_smem;
+  });
+  for (int i : idx) {
+    nys_solver* w = runs[i].h;
+    CK(cudaEventRecord(w->ev_req, w->st));
+    CK(cudaStreamWaitEvent(master->st, w->ev_req, 0));
+  }
+  CK(cudaEventRecord(master->ev_b0, master->st));
+  size_t g0 = 0;
+  while (g0 < idx.size()) {
+    size_t g1 = g0;
+    ClusterPlan gp = slots[idx[g0]].plan;
+    while (g1 < idx.size() && slots[idx[g1]].plan.C == gp.C && slots[idx[g1]].plan.a_smem == gp.a_smem) {
+      gp.smem_bytes = std::max(gp.smem_bytes, slots[idx[g1]].plan.smem_bytes);
+      ++g1;
+    }
+    for (size_t k = g0; k < g1; ++k) {
+      IpmRun& run = runs[idx[k]];
+      nys_solver* w = run.h;
+      const PcgRequest& q = run.req;
+      ClusterPcgTask& t = master->h_tasks[k];
+      t = ClusterPcgTask{};
+      t.m = run.m; t.n = run.n; t.ell = run.ell; t.ld = w->ld; t.lda = q.lda;
+      t.A = q.A; t.D = q.D; t.U = w->U; t.lam = w->lamh; t.xi = q.xi;
+      t.delta = q.delta; t.eta2 = q.eta * q.eta; t.max_iter = q.max_iter; t.forced = q.forced;
+      t.x = q.out; t.iters = w->si + SI_ITERS; t.sd = w->sd; t.err = w->si + SI_ERR;
+    }
+    CK(cudaMemcpyAsync(master->d_tasks + g0, master->h_tasks + g0, sizeof(ClusterPcgTask) * (g1 - g0),
+                       cudaMemcpyHostToDevice, master->st));
+    CK(pcg_cluster_f64(master->st, gp, master->h_tasks[g0], master->d_tasks + g0, (int)(g1 - g0)));
+    g0 = g1;
+  }
+  CK(cudaEventRecord(master->ev_b1, master->st));
+  for (int i : idx) {
+    CK(cudaStreamWaitEvent(runs[i].h->st, master->ev_b1, 0));
+    slots[i].batched = true;
+  }
+  launched = true;
+  return NYS_OK;
+}
+
+// After the rendezvous: the outcome of a shared-launch request (read like a
+// one-launch route), or the request served on the worker's own route.
+void finish_request(IpmRun& run, BatchSlot& slot) {
+  PcgRequest& q = run.req;
+  if (!q.active || run.done) return;
+  if (!slot.batched) {
+    serve_single(run);
+    return;
+  }
+  nys_solver* h = run.h;
+  slot.batched = false;
+  int rc = sync_scalars(h, 0);
+  if (rc != NYS_OK) { q.rc = rc; return; }
+  q.iters = h->h_si[SI_ITERS];
+  slot.acct_iters = std::max(q.iters, 1);
+  q.rc = NYS_OK;
+  if (q.forced < 0 && q.iters >= q.max_iter) {
+    if (cudaMemcpyAsync(h->h_red, h->sd, sizeof(double) * SD_COUNT, cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess) {
+      q.rc = fail(h, NYS_ERR_CUDA, "reading a batched PCG outcome failed");
+      return;
+    }
+    if (!(h->h_red[SD_RR] <= h->h_red[SD_ETA2] * h->h_red[SD_BNORM2])) q.rc = NYS_WARN_PCG_MAXITER;
+  }
+}
+
 extern "C" {
 
 void nys_default_options(nys_options* o) {
@@ -693,7 +1174,9 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
     cudaMemsetAsync(h->lp_arena, 0, h->lp_bytes, h->st);
   }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&h->ev_pcg0) != cudaSuccess || cudaEventCreate(&h->ev_pcg1) != cudaSuccess) {
+      cudaEventCreate(&h->ev_pcg0) != cudaSuccess || cudaEventCreate(&h->ev_pcg1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_req, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&h->ev_b0) != cudaSuccess || cudaEventCreate(&h->ev_b1) != cudaSuccess) {
     cudaFree(h->arena);
     delete h;
     return NYS_ERR_CUDA;
@@ -725,6 +1208,11 @@ int nys_destroy(nys_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ev_pcg0) cudaEventDestroy(h->ev_pcg0);
   if (h->ev_pcg1) cudaEventDestroy(h->ev_pcg1);
+  if (h->ev_req) cudaEventDestroy(h->ev_req);
+  if (h->ev_b0) cudaEventDestroy(h->ev_b0);
+  if (h->ev_b1) cudaEventDestroy(h->ev_b1);
+  if (h->d_tasks) cudaFree(h->d_tasks);
+  if (h->h_tasks) cudaFreeHost(h->h_tasks);
   cudaFree(h->arena);
   if (h->lp_arena) cudaFree(h->lp_arena);
   if (h->stage) cudaFree(h->stage);
@@ -871,25 +1359,73 @@ int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result*
     h->workers.push_back(w);
     h->worker_streams.push_back(s);
   }
-  // largest problems first (longest-processing-time order keeps the tail
-  // short); every launch shape depends on the problem alone, so a batched
-  // solve gives the same bits as a sequential one
+  if (h->task_cap < want) {
+    if (h->d_tasks) cudaFree(h->d_tasks);
+    if (h->h_tasks) cudaFreeHost(h->h_tasks);
+    h->d_tasks = nullptr;
+    h->h_tasks = nullptr;
+    h->task_cap = 0;
+    CK(cudaMalloc(&h->d_tasks, sizeof(ClusterPcgTask) * want));
+    CK(cudaMallocHost(&h->h_tasks, sizeof(ClusterPcgTask) * want));
+    h->task_cap = want;
+  }
+  // largest problems first, in lock-step groups of `want`: similar sizes meet
+  // at the same rendezvous; every launch shape depends on the problem alone,
+  // so a problem gets the same bits in any group
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (long long)p[a].m * p[a].n > (long long)p[b].m * p[b].n;
   });
-  std::atomic<int> next{0};
-  std::vector<std::thread> pool;
-  pool.reserve(want);
-  for (int t = 0; t < want; ++t) {
-    pool.emplace_back([&, t]() {
-      cudaSetDevice(h->device);
-      nys_solver* w = h->workers[t];
-      for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) nys_solve(w, &p[order[k]], &r[order[k]]);
-    });
+  for (int g0 = 0; g0 < count; g0 += want) {
+    const int G = std::min(want, count - g0);
+    std::vector<IpmRun> runs(G);
+    std::vector<BatchSlot> slots(G);
+    Rendezvous bar;
+    bar.n = G;
+    bool launched = false, any_active = true;
+    int launch_err = NYS_OK;
+    auto serve = [&]() {
+      const int rc = serve_batch(h, runs, slots, launched);
+      if (rc != NYS_OK && launch_err == NYS_OK) launch_err = rc;
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(G);
+    for (int t = 0; t < G; ++t) {
+      pool.emplace_back([&, t]() {
+        cudaSetDevice(h->device);
+        IpmRun& run = runs[t];
+        BatchSlot& slot = slots[t];
+        const int pi = order[g0 + t];
+        const bool started = run.start(h->workers[t], &p[pi], &r[pi]) == NYS_OK;
+        if (!started) r[pi].status = run.status;
+        slot.has_plan = started && !run.lp && pcg_cluster_plan(run.m, run.n, run.ell, 2, &slot.plan);
+        auto phase = [&](int which) {      // 0 top, 1 mid, 2 bottom
+          if (run.done) return;
+          const int rc = which == 0 ? run.top() : which == 1 ? run.mid() : run.bottom();
+          if (rc < 0 && !run.done) run.stop(rc);
+        };
+        while (true) {
+          phase(0);
+          bar.arrive([&] {
+            serve();
+            any_active = false;
+            for (auto& x : runs) any_active = any_active || !x.done;
+          });
+          if (!any_active) break;
+          if (launch_err != NYS_OK && slot.batched) { run.stop(launch_err); slot.batched = false; }
+          finish_request(run, slot);
+          phase(1);
+          bar.arrive(serve);
+          if (launch_err != NYS_OK && slot.batched) { run.stop(launch_err); slot.batched = false; }
+          finish_request(run, slot);
+          phase(2);
+        }
+        if (started) run.finish();
+      });
+    }
+    for (auto& th : pool) th.join();
   }
-  for (auto& th : pool) th.join();
   int worst_err = NYS_OK, worst_warn = NYS_OK;
   for (int i = 0; i < count; ++i) {
     if (r[i].status < worst_err) worst_err = r[i].status;
@@ -985,227 +1521,21 @@ int nys_step_length(nys_handle h, int n, const double* v, const double* dv, doub
 
 int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   if (!h) return NYS_ERR_ARG;
-  const auto t0 = std::chrono::steady_clock::now();
-  if (!p || !r) return fail(h, NYS_ERR_ARG, "nys_solve: null problem or result");
-  const int m = p->m, n = p->n;
-  const nys_options& o = h->opt;
-  const int lp = o.precision_mode == 1;
-  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n ||
-      p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 ||
-      !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0 || p->ell < 0)
-    return fail(h, NYS_ERR_ARG, "nys_solve: bad problem (sizes, dtype for the precision mode, or null pointers)");
-  const int ell = std::min(std::min(h->ell_cap, m), p->ell > 0 ? p->ell : h->ell_cap);
-  const long long lda = p->lda;
-  r->status = NYS_OK;
-  r->ipm_iters = 0;
-  r->pcg_iters_total = 0;
-  r->refine_steps = 0;
-  r->pcg_log_len = 0;
-  r->pcg_seconds = 0.0;
-  h->pcg_ms = 0.0;
-
-  // Problem data on the device (staged when the caller passes host memory).
-  const size_t esz = lp ? sizeof(float) : sizeof(double);
-  const void* Av = p->A;
-  const double *b = p->b, *c = p->c, *q = p->q;
-  if (p->host) {
-    const size_t a_bytes = align_up((size_t)m * lda * esz, 256);
-    const size_t need = a_bytes + 3 * align_up(sizeof(double) * (size_t)n, 256) +
-                        align_up(sizeof(double) * (size_t)m, 256);
-    if (need > h->stage_bytes) {
-      if (h->stage) cudaFree(h->stage);
-      h->stage = nullptr;
-      h->stage_bytes = 0;
-      if (cudaMalloc(&h->stage, need) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, NYS_ERR_NOMEM, "nys_solve: cannot stage a host problem of %zu bytes", need);
-      }
-      h->stage_bytes = need;
-    }
-    char* s = static_cast<char*>(h->stage);
-    void* dA = s;
-    double* db = reinterpret_cast<double*>(s + a_bytes);
-    double* dc = reinterpret_cast<double*>(s + a_bytes + align_up(sizeof(double) * m, 256));
-    double* dq = reinterpret_cast<double*>(reinterpret_cast<char*>(dc) + align_up(sizeof(double) * n, 256));
-    CK(cudaMemcpyAsync(dA, p->A, (size_t)m * lda * esz, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(db, p->b, sizeof(double) * m, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(dc, p->c, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(dq, p->q, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
-    Av = dA; b = db; c = dc; q = dq;
+  IpmRun run;
+  if (run.start(h, p, r) != NYS_OK) return run.status;
+  // a phase that returns an error without ending the run hit a CUDA failure:
+  // leave at once, as every other entry point does
+  int rc = NYS_OK;
+  while (!run.done) {
+    if ((rc = run.top()) < 0 && !run.done) return rc;
+    if (run.done) break;
+    if (run.req.active) serve_single(run);
+    if ((rc = run.mid()) < 0 && !run.done) return rc;
+    if (run.done) break;
+    if (run.req.active) serve_single(run);
+    if ((rc = run.bottom()) < 0 && !run.done) return rc;
   }
-  Prob P{m, n, lp, lp ? nullptr : static_cast<const double*>(Av), lp ? static_cast<const float*>(Av) : nullptr, lda};
-  const double* A = P.A64;
-  h->lp_bf16_stage = true;
-  if (lp)   // BF16 A and A^T for the inner solves and the sketch, FP32 A^T for residuals
-    CK(convert_transpose(h->st, m, n, 0, Av, lda, h->Ab, h->ld_b, h->AbT, h->ld_bt, h->AfT, h->ld_ft));
-  const cudaMemcpyKind kin = p->host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(h->x, p->x0, sizeof(double) * n, kin, h->st));
-  CK(cudaMemcpyAsync(h->y, p->y0, sizeof(double) * m, kin, h->st));
-  CK(cudaMemcpyAsync(h->z, p->z0, sizeof(double) * n, kin, h->st));
-  if (p->lam0) CK(cudaMemcpyAsync(h->lam, p->lam0, sizeof(double) * m, kin, h->st));
-  else CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
-  if (p->zeta0) CK(cudaMemcpyAsync(h->zeta, p->zeta0, sizeof(double) * n, kin, h->st));
-  else CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-  CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
-  CK(dot_f64(h->st, m, b, b, h->red_out + 8, h->red));
-  CK(dot_f64(h->st, n, c, c, h->red_out + 9, h->red));
-  int rc = sync_scalars(h, 10);
-  if (rc != NYS_OK) return r->status = rc;
-  const double bnorm = std::sqrt(h->h_red[8]), cnorm = std::sqrt(h->h_red[9]);
-
-  double rho = o.rho0, delta = o.delta0;
-  double mu = 0.0, mu_prev = 0.0;
-  double rel_p = 0.0, rel_d = 0.0;
-  int forced_idx = 0;
-  int warn = NYS_OK;
-  int k = 0;
-  int status = NYS_WARN_MAXITER;
-  auto next_forced = [&]() -> int {
-    if (o.forced_pcg_iters && forced_idx < o.n_forced_pcg) return o.forced_pcg_iters[forced_idx++];
-    return -1;
-  };
-  auto log_pcg = [&](int it) {
-    r->pcg_iters_total += it;
-    if (r->pcg_log && r->pcg_log_len < r->pcg_log_cap) r->pcg_log[r->pcg_log_len++] = it;
-  };
-
-  while (true) {
-    // Residuals and duality measure at the current iterate.
-    rc = op_Ax(h, P, h->x, 0.0, nullptr, h->Ax);
-    if (rc == NYS_OK) rc = op_Aty(h, P, h->y, nullptr, h->Aty);
-    if (rc != NYS_OK) { status = rc; break; }
-    CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
-                         rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
-    rc = sync_scalars(h, 3);
-    if (rc != NYS_OK) { status = rc; break; }
-    const double nrd = std::sqrt(h->h_red[0]), nrp = std::sqrt(h->h_red[2]);
-    mu = h->h_red[1] / n;
-    if (!std::isfinite(nrd) || !std::isfinite(nrp) || !std::isfinite(mu)) {
-      status = fail(h, NYS_ERR_NUMERIC, "non-finite residual at IPM iteration %d", k);
-      break;
-    }
-    rel_p = nrp / (1.0 + bnorm);
-    rel_d = nrd / (1.0 + cnorm);
-    if (k > 0) {
-      // PMM parameter update (reading of PEU): re-centre the proximal
-      // estimates on the iterate and decay rho, delta with the change of mu.
-      const double den = std::max(mu_prev, mu);
-      const double r_mu = den > 0.0 ? std::fabs(mu - mu_prev) / den : 0.0;
-      CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
-      CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-      delta = std::max(o.reg_floor, (1.0 - r_mu) * delta);
-      rho = std::max(o.reg_floor, (1.0 - r_mu) * rho);
-      // predictor right-hand sides with the updated PMM parameters
-      CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
-                           rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
-    }
-    // Termination (reading of TC: relative infeasibilities and mu).
-    if (o.forced_ipm_iters >= 0) {
-      if (k >= o.forced_ipm_iters) {
-        status = (rel_p <= o.tol && rel_d <= o.tol && mu <= o.tol) ? NYS_OK : NYS_WARN_MAXITER;
-        break;
-      }
-    } else if (rel_p <= o.tol && rel_d <= o.tol && mu <= o.tol) {
-      status = NYS_OK;
-      break;
-    }
-    if (k >= o.max_ipm_iter) { status = NYS_WARN_MAXITER; break; }
-
-    // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).
-    auto tk0 = std::chrono::steady_clock::now();
-    CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
-    rc = op_sketch(h, P, p->k0 + k, ell, h->D);
-    if (rc != NYS_OK) { status = rc; break; }
-    CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
-                        h->cw, h->num_sms));
-    const double eta = std::max(1e-10, std::min(1e-2, 0.1 * mu));
-    double t_pre = 0.0;
-    if (h->trace) {
-      cudaStreamSynchronize(h->st);
-      t_pre = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
-    }
-    const int pcg_before = r->pcg_iters_total, ref_before = r->refine_steps;
-
-    // Predictor (Algorithm 5, first step).
-    int it = 0, ref = 0;
-    if (lp)
-      rc = newton_lp(h, P, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, eta, o.max_pcg_iter,
-                     h->dxp, h->dyp, h->dzp, &it, &ref);
-    else
-      rc = newton(h, m, n, A, lda, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, h->U, h->ld,
-                  h->lamh, eta, o.max_pcg_iter, next_forced(), h->dxp, h->dyp, h->dzp, &it);
-    r->refine_steps += ref;
-    if (rc < 0) { status = rc; break; }
-    if (rc > 0) warn = rc;
-    log_pcg(it);
-    CK(step_ratios_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, h->red_out, h->red));
-    rc = sync_scalars(h, 2);
-    if (rc != NYS_OK) { status = rc; break; }
-    const double ap_bar = 0.995 * std::min(1.0, h->h_red[0]);
-    const double ad_bar = 0.995 * std::min(1.0, h->h_red[1]);
-    CK(mu_aff_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, ap_bar, ad_bar, h->red_out, h->red));
-    rc = sync_scalars(h, 1);
-    if (rc != NYS_OK) { status = rc; break; }
-    const double mu_aff = h->h_red[0] / n;
-    const double mu_t = mu_aff * mu_aff * mu_aff / (mu * mu);
-
-    // Corrector (Eq. corrector-RHS): r_d = r_p = 0, r_xz = mu_t - dxp dzp.
-    CK(corrector_rhs_f64(h->st, n, mu_t, h->dxp, h->dzp, h->r_xz));
-    if (lp)
-      rc = newton_lp(h, P, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, eta, o.max_pcg_iter,
-                     h->dxc, h->dyc, h->dzc, &it, &ref);
-    else
-      rc = newton(h, m, n, A, lda, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, h->U, h->ld,
-                  h->lamh, eta, o.max_pcg_iter, next_forced(), h->dxc, h->dyc, h->dzc, &it);
-    r->refine_steps += ref;
-    if (rc < 0) { status = rc; break; }
-    if (rc > 0) warn = rc;
-    log_pcg(it);
-    CK(add_dirs_f64(h->st, m, n, h->dxp, h->dyp, h->dzp, h->dxc, h->dyc, h->dzc));
-    CK(step_ratios_f64(h->st, n, h->x, h->dxc, h->z, h->dzc, h->red_out, h->red));
-    rc = sync_scalars(h, 2);
-    if (rc != NYS_OK) { status = rc; break; }
-    const double ap = 0.995 * std::min(1.0, h->h_red[0]);
-    const double ad = 0.995 * std::min(1.0, h->h_red[1]);
-    CK(ipm_update_f64(h->st, m, n, ap, ad, h->dxc, h->dyc, h->dzc, h->x, h->y, h->z));
-    if (h->trace) {
-      cudaStreamSynchronize(h->st);
-      const double t_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
-      std::fprintf(stderr,
-                   "[nys] k=%d mu=%.3e rel_p=%.3e rel_d=%.3e rho=%.2e delta=%.2e ap=%.3f ad=%.3f pcg=%d "
-                   "refine=%d sketch+core=%.1fms jacobi_sweeps=%d iter=%.1fms\n",
-                   k, mu, rel_p, rel_d, rho, delta, ap, ad, r->pcg_iters_total - pcg_before,
-                   r->refine_steps - ref_before, 1e3 * t_pre, h->h_si[SI_SWEEPS], 1e3 * t_it);
-    }
-    mu_prev = mu;
-    ++k;
-  }
-
-  // Outputs and final measures.
-  const cudaMemcpyKind kout = p->host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(r->x, h->x, sizeof(double) * n, kout, h->st));
-  CK(cudaMemcpyAsync(r->y, h->y, sizeof(double) * m, kout, h->st));
-  CK(cudaMemcpyAsync(r->z, h->z, sizeof(double) * n, kout, h->st));
-  if (r->lam) CK(cudaMemcpyAsync(r->lam, h->lam, sizeof(double) * m, kout, h->st));
-  if (r->zeta) CK(cudaMemcpyAsync(r->zeta, h->zeta, sizeof(double) * n, kout, h->st));
-  CK(objective_terms_f64(h->st, m, n, q, c, b, h->x, h->y, h->z, h->red_out + 4, h->red));
-  int rc2 = sync_scalars(h, 8);
-  const double xqx = h->h_red[4], cx = h->h_red[5], by = h->h_red[6];
-  const double pobj = 0.5 * xqx + cx, dobj = by - 0.5 * xqx;
-  r->ipm_iters = k;
-  r->rel_primal = rel_p;
-  r->rel_dual = rel_d;
-  r->mu = mu;
-  r->rel_gap = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj));
-  r->rho = rho;
-  r->delta = delta;
-  if (status == NYS_OK && warn != NYS_OK) status = warn;
-  if (status >= 0 && rc2 != NYS_OK) status = rc2;
-  if (status >= 0 && h->h_red[7] != 0.0) status = fail(h, NYS_ERR_NUMERIC, "non-finite final iterate");
-  r->status = status;
-  r->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  r->pcg_seconds = h->pcg_ms * 1e-3;
-  return status;
+  return run.finish();
 }
 
 }  // extern "C"
