@@ -47,6 +47,12 @@ WORKLOADS = {
                                         "BF16, FP32/float-float refinement, ell=400, tol 1e-6"),
     "precision-4000x20000": dict(form="bf16", m=4000, n=20000, ell=80, tol=1e-6, gen="device-exp200",
                                  desc="m=4000, n=20000 (scaled precision workload), ell=80, tol 1e-6"),
+    "precision-fp8-4000x20000": dict(form="fp8", m=4000, n=20000, ell=80, tol=1e-6, gen="device-exp200",
+                                     desc="m=4000, n=20000 (scaled precision workload), FP32 A stored FP8 "
+                                          "E4M3 with per-row scales for the inner PCG, ell=80, tol 1e-6"),
+    "precision-fp8-20000x100000": dict(form="fp8", m=20000, n=100000, ell=400, tol=1e-6, gen="device-exp200",
+                                       desc="m=20000, n=100000, sigma_i=exp(-i/200)+1e-3, FP32 A stored FP8 "
+                                            "E4M3 + row scales (inner PCG), BF16 sketch, ell=400, tol 1e-6"),
     "batch-256": dict(form="batch", count=256, ell=32, tol=1e-6, gen="batch",
                       desc="256 QPs, m~U{64..1024}, n~U{4m..8m}, sigma_i=1/i, q~U[0,1], "
                            "ell=min(32, m/4), tol 1e-6, FP64 form, nys_solve_batched"),
@@ -317,7 +323,7 @@ def main():
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=32, stream=stream)
         else:
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream,
-                           precision_mode=1 if form == "bf16" else 0)
+                           precision_mode={"bf16": 1, "fp8": 2}.get(form, 0))
 
         def step():
             if form == "batch":
@@ -368,12 +374,12 @@ def main():
         m0, n0 = A0.shape
         hbm_peak, bf16_peak, peak_src = measured_peaks()
         routes = sorted({nys.ROUTE_NAMES[nys.nys_pcg_route(h, pr[0].shape[0], pr[0].shape[1], pr[7])]
-                         for pr in dev_probs}) if form != "bf16" else ["graph"]
+                         for pr in dev_probs}) if form not in ("bf16", "fp8") else ["graph"]
         pcg_iters = sum(i["pcg_iters_total"] for i in timed)
         pcg_s = sum(i["pcg_seconds"] for i in timed)
         pcg = {"routes": routes, "iters": pcg_iters, "device_s": pcg_s,
                "us_per_iter": 1e6 * pcg_s / max(pcg_iters, 1)}
-        if form != "bf16" and "graph" not in routes and pcg_s > 0:
+        if form not in ("bf16", "fp8") and "graph" not in routes and pcg_s > 0:
             # one launch per PCG solve (thread-block cluster or cooperative grid):
             # that kernel dominates; its algorithmic FP64 work per iteration is
             # the operator (4 m n), the preconditioner (4 m ell) and the CG
@@ -396,11 +402,20 @@ def main():
                         "kernel": "BF16 normal-equations operator (k_rows<bf16> over A^T and A)",
                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})", "op_ms": op_s * 1e3,
                         "algorithmic_bytes": bytes_alg}
+        elif form == "fp8":
+            # FP8 operator: E4M3 A^T pass + A pass with row scales, FP32 accumulation
+            bytes_alg = 2.0 * m0 * n0 * 1 + 4.0 * (4 * m0 + 2 * n0)
+            op_s = time_fp8_operator(nys, h, A0, stream)
+            roofline = {"bound": "hbm", "achieved": bytes_alg / op_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": bytes_alg / op_s / 1e9 / hbm_peak, "traffic": None,
+                        "kernel": "FP8 normal-equations operator (k_rows<e4m3> over Q^T and Q, row scales)",
+                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})", "op_ms": op_s * 1e3,
+                        "algorithmic_bytes": bytes_alg}
         else:
             roofline = fp64_operator_roofline(nys, h, A0, stream)
         # ---- e2e: the same solves through the C ABI from pinned host buffers
         e2e = None
-        if form in ("fp64", "bf16"):
+        if form in ("fp64", "bf16", "fp8"):
             pin = lambda t: t.detach().cpu().pin_memory()
             hp = [tuple(pin(t) for t in pr[:7]) for pr in dev_probs]
             nys.nys_solve(h, *hp[0])
@@ -426,7 +441,7 @@ def main():
         gemv = operator_rooflines(nys, dev, stream) if (rank == 0 and not args.no_gemv) else None
 
         fp64_cmp = None
-        if form == "bf16" and args.compare_fp64:
+        if form in ("bf16", "fp8") and args.compare_fp64:
             A64 = dev_probs[0][0].double()
             h64 = nys.Handle(m0, n0, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream)
             t0 = time.perf_counter()
@@ -456,7 +471,8 @@ def main():
             "metric": "QP solves/s to KKT tol", "value": value, "unit": "QP solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "bf16": "bf16", "batch": "f64", "diff": "f64"}[form], "data": "synthetic",
+            "dtype": {"fp64": "f64", "bf16": "bf16", "fp8": "fp8e4m3", "batch": "f64", "diff": "f64"}[form],
+            "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6
@@ -560,9 +576,9 @@ def fp64_operator_roofline(nys, h, A0, stream, reps=50):
 
 
 def operator_rooflines(nys, dev, stream):
-    """The two operator GEMV pairs at the large workload shapes (inputs far
-    larger than L2, random entries): FP64 at m=5000, n=20000 and BF16 at
-    m=20000, n=100000."""
+    """The operator GEMV pairs at the large workload shapes (inputs far larger
+    than L2, random entries): FP64 at m=5000, n=20000, BF16 and FP8 (E4M3,
+    row scales) at m=20000, n=100000."""
     import torch
     out = {}
     g = torch.Generator(device=dev).manual_seed(0)
@@ -573,8 +589,13 @@ def operator_rooflines(nys, dev, stream):
         h.close()
         del A
         m, n = 20000, 100000
-        A = torch.randn(m, n, generator=g, device=dev, dtype=torch.bfloat16)
-        AT = A.T.contiguous()
+        A32 = torch.randn(m, n, generator=g, device=dev, dtype=torch.float32)
+        h8 = nys.Handle(m, n, ell=8, precision_mode=2, stream=stream)
+        op8_s = time_fp8_operator(nys, h8, A32, stream)
+        h8.close()
+        A = A32.to(torch.bfloat16)
+        AT = A32.T.contiguous().to(torch.bfloat16)
+        del A32
         h = nys.Handle(m, n, ell=8, precision_mode=1, stream=stream)
         D = torch.rand(n, dtype=torch.float64, device=dev) + 0.5
         v = torch.randn(m, dtype=torch.float64, device=dev)
@@ -596,8 +617,34 @@ def operator_rooflines(nys, dev, stream):
     out["bf16_20000x100000"] = {"bound": "hbm", "achieved": bytes_alg / op_s / 1e9, "peak": hbm_peak,
                                 "unit": "GB/s", "frac": bytes_alg / op_s / 1e9 / hbm_peak, "op_ms": op_s * 1e3,
                                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
+    b8 = 2.0 * m * n + 4.0 * (4 * m + 2 * n)
+    out["fp8_20000x100000"] = {"bound": "hbm", "achieved": b8 / op8_s / 1e9, "peak": hbm_peak,
+                               "unit": "GB/s", "frac": b8 / op8_s / 1e9 / hbm_peak, "op_ms": op8_s * 1e3,
+                               "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
     torch.cuda.empty_cache()
     return out
+
+
+def time_fp8_operator(nys, h, A32, stream, reps=20):
+    """Average duration of the FP8 operator pair (E4M3 copies with row scales
+    made by the library from the FP32 A), CUDA events on `stream`."""
+    import torch
+    dev = A32.device
+    m, n = A32.shape
+    Q, QT, sc = nys.nys_quantize_fp8(h, A32)
+    D = torch.rand(n, dtype=torch.float64, device=dev) + 0.5
+    v = torch.randn(m, dtype=torch.float64, device=dev)
+    out = torch.empty_like(v)
+    for _ in range(3):
+        nys.nys_normal_matvec_fp8(h, m, n, Q, QT, sc, D, 1e-3, v, out)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(reps):
+        nys.nys_normal_matvec_fp8(h, m, n, Q, QT, sc, D, 1e-3, v, out)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    del Q, QT
+    return f0.elapsed_time(f1) / reps / 1e3
 
 
 def time_lp_operator(nys, h, A32, stream):

@@ -54,7 +54,10 @@ typedef struct {
     int max_ipm_iter;
     int max_pcg_iter;
     unsigned long long seed;      /* key of the counter-based Gaussian stream         */
-    int precision_mode;           /* 0 = FP64 form (A must be NYS_F64)                */
+    int precision_mode;           /* 0 = FP64 form (A must be NYS_F64); 1 = precision */
+                                  /*   form, BF16 inner operator; 2 = precision form, */
+                                  /*   FP8 E4M3 inner operator with per-row scales    */
+                                  /*   (1 and 2: A must be NYS_F32)                   */
     double rho0, delta0, reg_floor;
     /* Parity mode (optional, host arrays): run exactly forced_pcg_iters[s] PCG
      * iterations in Newton solve s (predictor, corrector, predictor, ...), and
@@ -105,7 +108,9 @@ typedef struct {
     double rho, delta;            /* final PMM regularisation                          */
     double seconds;               /* wall time inside nys_solve                        */
     double pcg_seconds;           /* device time of the PCG solves (CUDA events on the */
-                                  /*   handle's stream around each solve)              */
+                                  /*   handle's stream around each solve; in a batch,  */
+                                  /*   each problem's share of the launches it shared, */
+                                  /*   in proportion to its PCG iterations)            */
     int* pcg_log;                 /* optional host array: PCG iterations per Newton   */
     int pcg_log_cap;              /*   solve, in order (capacity in entries)           */
     int pcg_log_len;              /* entries written                                   */
@@ -187,6 +192,25 @@ int nys_normal_matvec(nys_handle h, int m, int n, int a_dtype, const void* A, lo
 int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
                          const void* AT, long long ldat, const double* D, double delta, const double* v,
                          double* out);
+
+/* FP8 storage of the precision form's matrix (the brief's "FP8 with per-row
+ * scales" variant of Eq. normal-eq's operator): s_r = max_c |A[r, c]| / 448
+ * (448 = the largest finite E4M3 value; s_r = 1 for an all-zero row) and
+ * Q[r, c] = E4M3(A[r, c] / s_r), round to nearest, saturating, so that
+ * A ~ diag(s) Q.  A: FP32 device m x n (lda >= n).  Outputs (device,
+ * caller-allocated): Q, m x ldq bytes (ldq >= n); QT = Q^T, n x ldqt bytes
+ * (ldqt >= m); padding columns are zeroed; row_scale: FP32, m. */
+int nys_quantize_fp8(nys_handle h, int m, int n, const float* A, long long lda, void* Q, long long ldq,
+                     void* QT, long long ldqt, float* row_scale);
+
+/* out = diag(s) Q (D .* (Q^T (s .* v))) + delta v with (Q, QT, s) from
+ * nys_quantize_fp8: the FP8 operator of the inner PCG solves of
+ * precision_mode 2, FP32 products and sums.  Q, QT: device bytes, rows 16-byte
+ * aligned for the vectorised path (ldq, ldqt multiples of 16); D, v, out: FP64
+ * device.  The handle must have precision_mode 2. */
+int nys_normal_matvec_fp8(nys_handle h, int m, int n, const void* Q, long long ldq, const void* QT,
+                          long long ldqt, const float* row_scale, const double* D, double delta, const double* v,
+                          double* out);
 
 /* (N + delta I) v = A (D .* (A^T v)) + delta v, as nys_normal_matvec, for
  * callers that cannot allocate device memory (code running inside a stream

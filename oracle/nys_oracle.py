@@ -102,6 +102,58 @@ def sketch(A: np.ndarray, D: np.ndarray, Omega: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# FP8 storage of the precision form (the brief's per-row-scaled variant of the
+# operator of Eq. normal-eq): E4M3 = 1 sign, 4 exponent (bias 7), 3 mantissa
+# bits, no infinities, largest finite 448, subnormal spacing 2^-9.
+# ---------------------------------------------------------------------------
+
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest E4M3 value (ties to even mantissa), saturating at
+    +-448.  Works on the exact values of x (FP64 holds every input exactly)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    with np.errstate(divide="ignore"):
+        e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    e = np.clip(e, -6.0, 8.0)                  # below 2^-6: the subnormal spacing 2^-9
+    quantum = np.exp2(e - 3.0)                 # 3 mantissa bits
+    q = np.round(a / quantum) * quantum        # numpy rounds halves to even
+    q = np.minimum(q, E4M3_MAX)
+    return np.copysign(q, x)
+
+
+def e4m3_decode(bits: np.ndarray) -> np.ndarray:
+    """Values of E4M3 bit patterns (uint8)."""
+    b = np.asarray(bits, dtype=np.int64)
+    sgn = np.where(b >> 7, -1.0, 1.0)
+    ex = (b >> 3) & 15
+    man = b & 7
+    val = np.where(ex == 0, man / 8.0 * 2.0 ** -6, (1.0 + man / 8.0) * np.exp2(ex - 7.0))
+    val = np.where((ex == 15) & (man == 7), np.nan, val)
+    return sgn * val
+
+
+def fp8_rowscale_quantize(A32: np.ndarray):
+    """Per-row scales s_r = max_c |A_rc| / 448 (1 for a zero row), computed in
+    FP32 as stored, and the E4M3 values of A_rc / s_r (the division in FP32).
+    Returns (Qvalues FP64, s FP32) with A ~ diag(s) Q."""
+    A32 = np.asarray(A32, dtype=np.float32)
+    mx = np.max(np.abs(A32), axis=1)
+    s = np.where(mx > 0, mx / np.float32(E4M3_MAX), np.float32(1.0)).astype(np.float32)
+    ratio = (A32 / s[:, None]).astype(np.float32)
+    return e4m3_round(ratio.astype(np.float64)), s
+
+
+def fp8_normal_matvec(Q: np.ndarray, s: np.ndarray, D: np.ndarray, delta: float, v: np.ndarray) -> np.ndarray:
+    """The FP8 operator diag(s) Q (D .* (Q^T (s .* v))) + delta v in FP64."""
+    s = np.asarray(s, dtype=np.float64)
+    t = D * (Q.T @ (s * v))
+    return s * (Q @ t) + delta * v
+
+
+# ---------------------------------------------------------------------------
 # Randomized Nystrom approximation (Algorithm 1) and preconditioner
 # (Algorithm 2, Eq. Nys_precond_inv).
 # ---------------------------------------------------------------------------

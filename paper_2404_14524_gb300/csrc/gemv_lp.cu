@@ -6,7 +6,8 @@
 // every pass streams its matrix once, fully coalesced, 16 bytes per lane.
 //
 //   k_rows<T, R>   out[r] = scale[r] * sum_c M[r, c] x[c] (+ beta v[r])
-//                  T = BF16 or FP32 storage, FP32 products and accumulation;
+//                  T = FP8 (E4M3), BF16 or FP32 storage, FP32 products and
+//                  accumulation;
 //                  one warp owns R rows and reuses each 8-element chunk of x
 //                  for all R rows (x traffic is 1/R of the naive one).
 //   k_rows_ff<R>   the same with FP32 storage and a float-float (hi + lo)
@@ -17,6 +18,7 @@
 //                  accuracy at FP32 throughput: GB300 runs FP32 ~70x faster
 //                  than FP64.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -46,8 +48,39 @@ __device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
   v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
+// 16 FP8 E4M3 values (16 bytes) to FP32
+__device__ __forceinline__ void load16(const __nv_fp8_e4m3* p, float (&v)[16]) {
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  const __nv_fp8x2_storage_t* q = reinterpret_cast<const __nv_fp8x2_storage_t*>(&u);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q[i], __NV_E4M3);
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+// the same 16-element step for the 2- and 4-byte types (two 8-element loads)
+__device__ __forceinline__ void load16(const __nv_bfloat16* p, float (&v)[16]) {
+  float a[8], b[8];
+  load8(p, a);
+  load8(p + 8, b);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { v[i] = a[i]; v[8 + i] = b[i]; }
+}
+__device__ __forceinline__ void load16(const float* p, float (&v)[16]) {
+  float a[8], b[8];
+  load8(p, a);
+  load8(p + 8, b);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { v[i] = a[i]; v[8 + i] = b[i]; }
+}
+
 template <typename TA>
 __device__ __forceinline__ float load1(const TA* p);
+template <>
+__device__ __forceinline__ float load1<__nv_fp8_e4m3>(const __nv_fp8_e4m3* p) { return float(p[0]); }
 template <>
 __device__ __forceinline__ float load1<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
 template <>
@@ -66,23 +99,39 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
   const int lane = threadIdx.x & 31;
   const int r0 = (blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kRowsPerWarp;
   if (r0 >= rows) return;
-  // this block's column range (a multiple of 8 wide, except the last)
+  // this block's column range (a multiple of 16 wide, except the last)
   const int cb = blockIdx.y * cols_per_split;
   const int ce = min(cols, cb + cols_per_split);
   float acc[kRowsPerWarp];
 #pragma unroll
   for (int i = 0; i < kRowsPerWarp; ++i) acc[i] = 0.0f;
-  const int cvec = kVec ? cb + ((ce - cb) / 8) * 8 : cb;
-  for (int c = cb + lane * 8; c < cvec; c += 256) {
-    float xv[8];
-    load8(x + c, xv);
+  // 16 elements a lane per step for FP8 (one 16-byte load), 8 otherwise
+  constexpr int kE = sizeof(TA) == 1 ? 16 : 8;
+  const int cvec = kVec ? cb + ((ce - cb) / kE) * kE : cb;
+  for (int c = cb + lane * kE; c < cvec; c += 32 * kE) {
+    if constexpr (kE == 16) {
+      float xv[16];
+      load8(x + c, *reinterpret_cast<float(*)[8]>(xv));
+      load8(x + c + 8, *reinterpret_cast<float(*)[8]>(xv + 8));
 #pragma unroll
-    for (int i = 0; i < kRowsPerWarp; ++i) {
-      const int r = min(r0 + i, rows - 1);
-      float a[8];
-      load8(A + (long long)r * lda + c, a);
+      for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int r = min(r0 + i, rows - 1);
+        float a[16];
+        load16(A + (long long)r * lda + c, a);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i] = fmaf(a[j], xv[j], acc[i]);
+        for (int j = 0; j < 16; ++j) acc[i] = fmaf(a[j], xv[j], acc[i]);
+      }
+    } else {
+      float xv[8];
+      load8(x + c, xv);
+#pragma unroll
+      for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int r = min(r0 + i, rows - 1);
+        float a[8];
+        load8(A + (long long)r * lda + c, a);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i] = fmaf(a[j], xv[j], acc[i]);
+      }
     }
   }
   for (int c = cvec + lane; c < ce; c += 32) {
@@ -262,6 +311,46 @@ __global__ void k_convert_transpose(int rows, int cols, const TS* __restrict__ s
   }
 }
 
+// Per-row scales of an FP32 matrix for E4M3 storage: s_r = max_c |A[r, c]| / 448
+// (448 = the largest finite E4M3 value), 1 for an all-zero row; one warp per row.
+__global__ void k_row_scale_fp8(int rows, int cols, const float* __restrict__ A, long long lda,
+                                float* __restrict__ s32, double* __restrict__ s64) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  float mx = 0.0f;
+  for (int c = lane; c < cols; c += 32) mx = fmaxf(mx, fabsf(__ldg(A + (long long)r * lda + c)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    const float sc = mx > 0.0f ? mx / 448.0f : 1.0f;
+    s32[r] = sc;
+    s64[r] = (double)sc;
+  }
+}
+
+// Q[r, c] = E4M3(A[r, c] / s_r) (round to nearest, saturating) and its
+// transpose QT[c, r]; padding columns zeroed.  32 x 32 tiles.
+__global__ void k_quant_fp8(int rows, int cols, const float* __restrict__ A, long long lda,
+                            const float* __restrict__ s32, __nv_fp8_e4m3* __restrict__ Q, long long ldq,
+                            __nv_fp8_e4m3* __restrict__ QT, long long ldqt) {
+  __shared__ __nv_fp8_storage_t tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    __nv_fp8_storage_t q = 0;
+    if (r < rows && c < cols) q = __nv_cvt_float_to_fp8(__ldg(A + (long long)r * lda + c) / s32[r], __NV_SATFINITE, __NV_E4M3);
+    tile[k][tx] = q;
+    if (r < rows && c < ldq) reinterpret_cast<__nv_fp8_storage_t*>(Q)[(long long)r * ldq + c] = q;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;     // output row c of the transpose, column r
+    if (c < cols && r < ldqt) reinterpret_cast<__nv_fp8_storage_t*>(QT)[(long long)c * ldqt + r] = tile[tx][k];
+  }
+}
+
 int row_blocks(int rows) {
   const int per = kRowsPerWarp * kWarpsPerBlock;
   return (rows + per - 1) / per;
@@ -280,18 +369,28 @@ int col_splits(int rows, int cols, size_t part_cap) {
 
 }  // namespace
 
-cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_bf16, const void* A, long long lda,
+cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_type, const void* A, long long lda,
                          const float* x, const float* scale, double beta, const double* v, void* out,
                          int out_f64, const int* skip, const double* beta_dev, double* part, size_t part_cap) {
   if (rows <= 0) return cudaSuccess;
   const int S = part ? col_splits(rows, cols, part_cap) : 1;
-  const int cps = S > 1 ? ((cols + S - 1) / S + 7) / 8 * 8 : cols;
+  const int cps = S > 1 ? ((cols + S - 1) / S + 15) / 16 * 16 : cols;
   const int nsplit = (cols + cps - 1) / cps;
   double* pp = nsplit > 1 ? part : nullptr;
   dim3 grid(row_blocks(rows), nsplit);
   const int T = 32 * kWarpsPerBlock;
   count_launches(1);
-  if (a_bf16) {
+  if (a_type == kLpFp8) {
+    const bool vec = (lda % 16 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0);
+    const auto* a = static_cast<const __nv_fp8_e4m3*>(A);
+    if (out_f64) {
+      if (vec) k_rows<__nv_fp8_e4m3, double, true><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev, cps, pp);
+      else k_rows<__nv_fp8_e4m3, double, false><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (double*)out, skip, beta_dev, cps, pp);
+    } else {
+      if (vec) k_rows<__nv_fp8_e4m3, float, true><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev, cps, pp);
+      else k_rows<__nv_fp8_e4m3, float, false><<<grid, T, 0, st>>>(rows, cols, a, lda, x, scale, beta, v, (float*)out, skip, beta_dev, cps, pp);
+    }
+  } else if (a_type == kLpBf16) {
     const bool vec = (lda % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0);
     const auto* a = static_cast<const __nv_bfloat16*>(A);
     if (out_f64) {
@@ -369,6 +468,17 @@ cudaError_t convert_transpose(cudaStream_t st, int rows, int cols, int src_f64, 
     k_convert_transpose<double><<<grid, 256, 0, st>>>(rows, cols, (const double*)src, lds, dst, ldd, dstT, ldt, dstTf, ldtf);
   else
     k_convert_transpose<float><<<grid, 256, 0, st>>>(rows, cols, (const float*)src, lds, dst, ldd, dstT, ldt, dstTf, ldtf);
+  return cudaGetLastError();
+}
+
+cudaError_t quantize_fp8(cudaStream_t st, int rows, int cols, const float* A, long long lda, float* s32,
+                         double* s64, void* Q, long long ldq, void* QT, long long ldqt) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  count_launches(2);
+  k_row_scale_fp8<<<(rows + 7) / 8, 256, 0, st>>>(rows, cols, A, lda, s32, s64);
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_quant_fp8<<<grid, 256, 0, st>>>(rows, cols, A, lda, s32, static_cast<__nv_fp8_e4m3*>(Q), ldq,
+                                    static_cast<__nv_fp8_e4m3*>(QT), ldqt);
   return cudaGetLastError();
 }
 

@@ -102,11 +102,16 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
                              CoreWork cw, int num_sms);
 
 // ---------------------------------------------------------------- precision-form GEMVs
-// out[r] = scale[r] * sum_c A[r, c] x[c] + beta v[r]; A BF16 (a_bf16) or FP32
-// row-major, x/scale FP32, FP32 accumulation; out FP64 (out_f64) or FP32.
+// Storage types of the reduced-precision operator.
+constexpr int kLpFp32 = 0;
+constexpr int kLpBf16 = 1;
+constexpr int kLpFp8 = 2;     // E4M3 with per-row scales
+// out[r] = scale[r] * sum_c A[r, c] x[c] + beta v[r]; A row-major in FP32,
+// BF16 or FP8 E4M3 (a_type), x/scale FP32, FP32 accumulation; out FP64
+// (out_f64) or FP32.
 // With `part` (>= splits * rows doubles) short, wide matrices are split over
 // columns as well, with a fixed-order reduction of the partial sums.
-cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_bf16, const void* A, long long lda,
+cudaError_t gemv_rows_lp(cudaStream_t st, int rows, int cols, int a_type, const void* A, long long lda,
                          const float* x, const float* scale, double beta, const double* v, void* out,
                          int out_f64, const int* skip = nullptr, const double* beta_dev = nullptr,
                          double* part = nullptr, size_t part_cap = 0);
@@ -125,6 +130,12 @@ cudaError_t to_f32(cudaStream_t st, int n, int npad, const double* x, const doub
 cudaError_t convert_transpose(cudaStream_t st, int rows, int cols, int src_f64, const void* src, long long lds,
                               __nv_bfloat16* dst, long long ldd, __nv_bfloat16* dstT, long long ldt,
                               float* dstTf, long long ldtf);
+
+// FP8 E4M3 copies of a row-major FP32 matrix with per-row scales:
+// s_r = max_c |A[r, c]| / 448 (1 for a zero row), Q[r, c] = E4M3(A[r, c] / s_r)
+// (ldq >= cols, padding zeroed) and QT = Q^T (ldqt >= rows); s in FP32 and FP64.
+cudaError_t quantize_fp8(cudaStream_t st, int rows, int cols, const float* A, long long lda, float* s32,
+                         double* s64, void* Q, long long ldq, void* QT, long long ldqt);
 
 // ---------------------------------------------------------------- tcgen05 BF16 GEMM
 // part[z][c][r] = sum_{k in split z} A[r, k] B[c, k]; A: M x K, B: N x K, both
@@ -171,9 +182,11 @@ struct LpOperator {
   double* t64;                      // ff: FP64 scratch of n for D .* (A^T p)
   float *xh, *xl;                   // ff: hi/lo split scratch, max(m, n) padded
   int ld_npad;
-  int bf16;
+  int a_type;                       // kLpFp32, kLpBf16 or kLpFp8
   const void* A;  long long lda;    // m x n
   const void* AT; long long ldat;   // n x m
+  const float* rs32;                // kLpFp8: row scales of A (m), FP32
+  const double* rs64;               //   and FP64
   const float* Df;
   float* xf;
   float* tf;

@@ -309,13 +309,14 @@ cudaError_t pcg_iteration_lp(cudaStream_t st, int m, int n, const LpOperator& op
     if (e != cudaSuccess) return e;
     return pcg_tail(st, m, ell, U, ld, w, sd, si, red);
   }
-  // pf = FP32(p);  tf = Df .* (A^T pf);  w = A tf + delta p
-  cudaError_t e = to_f32(st, m, op.ld_mpad, w.p, nullptr, op.xf, done);
+  // pf = FP32(s .* p);  tf = Df .* (Q^T pf);  w = s .* (Q tf) + delta p, with
+  // s the per-row scales of FP8 storage (A = diag(s) Q) and s = 1 otherwise
+  cudaError_t e = to_f32(st, m, op.ld_mpad, w.p, op.rs64, op.xf, done);
   if (e != cudaSuccess) return e;
-  e = gemv_rows_lp(st, n, m, op.bf16, op.AT, op.ldat, op.xf, op.Df, 0.0, nullptr, op.tf, 0, done, nullptr, op.part,
+  e = gemv_rows_lp(st, n, m, op.a_type, op.AT, op.ldat, op.xf, op.Df, 0.0, nullptr, op.tf, 0, done, nullptr, op.part,
                    op.part_cap);
   if (e != cudaSuccess) return e;
-  e = gemv_rows_lp(st, m, n, op.bf16, op.A, op.lda, op.tf, nullptr, 1.0, w.p, w.w, 1, done, sd + SD_DELTA, op.part,
+  e = gemv_rows_lp(st, m, n, op.a_type, op.A, op.lda, op.tf, op.rs32, 1.0, w.p, w.w, 1, done, sd + SD_DELTA, op.part,
                    op.part_cap);
   if (e != cudaSuccess) return e;
   return pcg_tail(st, m, ell, U, ld, w, sd, si, red);

@@ -89,6 +89,13 @@ struct nys_solver {
   ClusterPlan cp;
   int gk_op = -1;            // graph key: operator kind
   double* pcg_x = nullptr;   // PCG solution buffer (copied out after each solve)
+  // FP8 variant (precision_mode 2): E4M3 copies of A and A^T with the
+  // per-row scales of A feed the inner PCG (the sketch keeps BF16)
+  void* A8 = nullptr;
+  void* A8T = nullptr;
+  float* rs32 = nullptr;
+  double* rs64 = nullptr;
+  long long ld_q = 0, ld_qt = 0;
   // precision form (precision_mode 1): A is FP32 (the problem definition);
   // BF16 copies of A and A^T feed the inner PCG and the tensor-core sketch,
   // an FP32 copy of A^T the refinement residual.
@@ -238,6 +245,14 @@ size_t carve_lp(nys_solver* h, char* base) {
   h->ecorr = c.take<double>(M);
   h->lp_part_cap = 16 * std::max(M, N);
   h->lp_part = c.take<double>(h->lp_part_cap);
+  if (h->opt.precision_mode == 2) {
+    h->ld_q = (long long)align_up(N, 16);
+    h->ld_qt = (long long)align_up(M, 16);
+    h->A8 = c.take<unsigned char>(M * (size_t)h->ld_q);
+    h->A8T = c.take<unsigned char>(N * (size_t)h->ld_qt);
+    h->rs32 = c.take<float>(M);
+    h->rs64 = c.take<double>(M);
+  }
   return c.off;
 }
 
@@ -284,7 +299,7 @@ struct OpSpec {
   const double* A;      // kind 0
   long long lda;
   const double* D;      // kind 0
-  LpOperator lp;        // kinds 1, 2
+  LpOperator lp;        // kinds 1-4 (BF16, FP32, float-float, FP8)
   const void* key() const { return kind == 0 ? (const void*)A : lp.A; }
 };
 
@@ -557,6 +572,8 @@ int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D) {
 // refinement contracts only while kappa * u_bf16 < 1).  Stage 2: one PCG solve
 // of the remaining residual on the float-float FP32 operator, which is the
 // problem's operator to ~1e-13, to the outer tolerance.
+// kind 1: BF16 copies; 4: FP8 copies with row scales; 2: the FP32 problem
+// matrix; 3: the FP32 matrix with float-float sums.
 LpOperator make_lp_op(nys_solver* h, const Prob& P, int kind, const double* D) {
   LpOperator op{};
   op.ff = kind == 3;
@@ -565,11 +582,15 @@ LpOperator make_lp_op(nys_solver* h, const Prob& P, int kind, const double* D) {
   op.xh = h->fh;
   op.xl = h->fl;
   op.ld_npad = (int)align_up(P.n, 8);
-  op.bf16 = kind == 1;
-  op.A = kind == 1 ? (const void*)h->Ab : (const void*)P.Af;
-  op.lda = kind == 1 ? h->ld_b : P.lda;
-  op.AT = kind == 1 ? (const void*)h->AbT : (const void*)h->AfT;
-  op.ldat = kind == 1 ? h->ld_bt : h->ld_ft;
+  op.a_type = kind == 1 ? kLpBf16 : kind == 4 ? kLpFp8 : kLpFp32;
+  if (kind == 1) {
+    op.A = h->Ab; op.lda = h->ld_b; op.AT = h->AbT; op.ldat = h->ld_bt;
+  } else if (kind == 4) {
+    op.A = h->A8; op.lda = h->ld_q; op.AT = h->A8T; op.ldat = h->ld_qt;
+    op.rs32 = h->rs32; op.rs64 = h->rs64;
+  } else {
+    op.A = P.Af; op.lda = P.lda; op.AT = h->AfT; op.ldat = h->ld_ft;
+  }
   op.Df = h->Df;
   op.xf = h->xf;
   op.tf = h->tf;
@@ -600,7 +621,7 @@ int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, co
   while (xin > 0.0 && rn > eta * xin) {
     const bool final_stage = !bf16_stage || steps >= max_bf16_steps;
     OpSpec op{};
-    op.kind = final_stage ? 3 : 1;
+    op.kind = final_stage ? 3 : (h->opt.precision_mode == 2 ? 4 : 1);
     op.lp = make_lp_op(h, P, op.kind, D);
     // inner tolerance relative to the current residual
     const double need = eta * xin / rn;
@@ -719,7 +740,7 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   if (!p || !r) { done = true; return status = fail(h, NYS_ERR_ARG, "nys_solve: null problem or result"); }
   m = p->m; n = p->n;
   const nys_options& o = h->opt;
-  lp = o.precision_mode == 1;
+  lp = o.precision_mode >= 1;
   if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n ||
       p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 ||
       !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0 || p->ell < 0) {
@@ -773,6 +794,9 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   h->lp_bf16_stage = true;
   if (lp)   // BF16 A and A^T for the inner solves and the sketch, FP32 A^T for residuals
     CK(convert_transpose(h->st, m, n, 0, Av, lda, h->Ab, h->ld_b, h->AbT, h->ld_bt, h->AfT, h->ld_ft));
+  if (o.precision_mode == 2)   // E4M3 A and A^T with A's row scales for the inner solves
+    CK(quantize_fp8(h->st, m, n, static_cast<const float*>(Av), lda, h->rs32, h->rs64, h->A8, h->ld_q, h->A8T,
+                    h->ld_qt));
   const cudaMemcpyKind kin = p->host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(h->x, p->x0, sizeof(double) * n, kin, h->st));
   CK(cudaMemcpyAsync(h->y, p->y0, sizeof(double) * m, kin, h->st));
@@ -1133,7 +1157,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   *out = nullptr;
   if (!opt || max_m <= 0 || max_n <= 0 || max_batch < 0 || opt->ell <= 0 || opt->tol <= 0.0 ||
       opt->max_ipm_iter < 0 || opt->max_pcg_iter < 0 || opt->precision_mode < 0 ||
-      opt->precision_mode > 1 || (opt->precision_mode == 1 && opt->ell > 512))
+      opt->precision_mode > 2 || (opt->precision_mode >= 1 && opt->ell > 512))
     return NYS_ERR_ARG;
   nys_solver* h = new nys_solver();
   h->opt = *opt;
@@ -1162,7 +1186,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
     delete h;
     return NYS_ERR_NOMEM;
   }
-  if (opt->precision_mode == 1) {
+  if (opt->precision_mode >= 1) {
     h->lp_bytes = carve_lp(h, nullptr);
     if (cudaMalloc(&h->lp_arena, h->lp_bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -1257,6 +1281,34 @@ int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A,
   CK(gemv_rows_lp(h->st, n, m, bf, AT, ldat, h->xf, h->Df, 0.0, nullptr, h->tf, 0, nullptr, nullptr, h->lp_part,
                   h->lp_part_cap));
   CK(gemv_rows_lp(h->st, m, n, bf, A, lda, h->tf, nullptr, delta, v, out, 1, nullptr, nullptr, h->lp_part,
+                  h->lp_part_cap));
+  return NYS_OK;
+}
+
+int nys_quantize_fp8(nys_handle h, int m, int n, const float* A, long long lda, void* Q, long long ldq,
+                     void* QT, long long ldqt, float* row_scale) {
+  if (!h) return NYS_ERR_ARG;
+  if (!h->rs64) return fail(h, NYS_ERR_ARG, "nys_quantize_fp8: not a precision_mode 2 handle");
+  if (m <= 0 || n <= 0 || m > h->max_m || lda < n || ldq < n || ldqt < m || !A || !Q || !QT || !row_scale)
+    return fail(h, NYS_ERR_ARG, "nys_quantize_fp8: bad argument");
+  CK(quantize_fp8(h->st, m, n, A, lda, row_scale, h->rs64, Q, ldq, QT, ldqt));
+  return NYS_OK;
+}
+
+int nys_normal_matvec_fp8(nys_handle h, int m, int n, const void* Q, long long ldq, const void* QT,
+                          long long ldqt, const float* row_scale, const double* D, double delta, const double* v,
+                          double* out) {
+  if (!h) return NYS_ERR_ARG;
+  if (!h->rs64) return fail(h, NYS_ERR_ARG, "nys_normal_matvec_fp8: not a precision_mode 2 handle");
+  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || ldq < n || ldqt < m || !Q || !QT || !row_scale || !D ||
+      !v || !out || out == v)
+    return fail(h, NYS_ERR_ARG, "nys_normal_matvec_fp8: bad argument");
+  CK(panel_f32_to_f64(h->st, m, 1, row_scale, m, h->rs64, m));
+  CK(to_f32(h->st, n, (int)align_up(n, 8), D, nullptr, h->Df));
+  CK(to_f32(h->st, m, (int)align_up(m, 8), v, h->rs64, h->xf));
+  CK(gemv_rows_lp(h->st, n, m, kLpFp8, QT, ldqt, h->xf, h->Df, 0.0, nullptr, h->tf, 0, nullptr, nullptr, h->lp_part,
+                  h->lp_part_cap));
+  CK(gemv_rows_lp(h->st, m, n, kLpFp8, Q, ldq, h->tf, row_scale, delta, v, out, 1, nullptr, nullptr, h->lp_part,
                   h->lp_part_cap));
   return NYS_OK;
 }

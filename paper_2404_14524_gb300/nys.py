@@ -88,6 +88,8 @@ _SIGS = {
     "nys_normal_matvec": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _P, _P]),
     "nys_normal_matvec_lp": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _D, _P, _P]),
     "nys_normal_matvec_noalloc": (_I, [_I, _I, _P, _LL, _P, _D, _P, _P, _P]),
+    "nys_quantize_fp8": (_I, [_P, _I, _I, _P, _LL, _P, _LL, _P, _LL, _P]),
+    "nys_normal_matvec_fp8": (_I, [_P, _I, _I, _P, _LL, _P, _LL, _P, _P, _D, _P, _P]),
     "nys_gaussian": (_I, [_P, ctypes.c_ulonglong, _I, _I, _I, _P, _I]),
     "nys_sketch": (_I, [_P, _I, _I, _I, _P, _LL, _P, _I, _P, _P, _I]),
     "nys_nystrom": (_I, [_P, _I, _I, _P, _P, _I, _P, _P, ctypes.POINTER(_D)]),
@@ -245,6 +247,29 @@ def nys_normal_matvec_lp(h: Handle, A, AT, D, delta: float, v, out=None):
     out = torch.empty_like(v) if out is None else out
     h.check(lib().nys_normal_matvec_lp(h.h, m, n, dt, _ptr(A), A.stride(0), _ptr(AT), AT.stride(0),
                                        _ptr(_f64(D, "D")), float(delta), _ptr(_f64(v, "v")), _ptr(_f64(out, "out"))))
+    return out
+
+
+def nys_quantize_fp8(h: Handle, A32):
+    """E4M3 copies of an FP32 row-major A (m x n) with per-row scales:
+    returns (Q, QT, row_scale); Q is m x round16(n) and QT n x round16(m)
+    uint8 tensors holding the E4M3 bits (padding zero), row_scale FP32."""
+    m, n = A32.shape
+    if A32.dtype != torch.float32:
+        raise TypeError("A must be float32")
+    ldq, ldqt = (n + 15) // 16 * 16, (m + 15) // 16 * 16
+    Q = torch.empty(m, ldq, dtype=torch.uint8, device=A32.device)
+    QT = torch.empty(n, ldqt, dtype=torch.uint8, device=A32.device)
+    s = torch.empty(m, dtype=torch.float32, device=A32.device)
+    h.check(lib().nys_quantize_fp8(h.h, m, n, _ptr(A32), A32.stride(0), _ptr(Q), ldq, _ptr(QT), ldqt, _ptr(s)))
+    return Q, QT, s
+
+
+def nys_normal_matvec_fp8(h: Handle, m: int, n: int, Q, QT, row_scale, D, delta: float, v, out=None):
+    """FP8 operator diag(s) Q (D .* (Q^T (s .* v))) + delta v (precision_mode 2 handle)."""
+    out = torch.empty_like(v) if out is None else out
+    h.check(lib().nys_normal_matvec_fp8(h.h, m, n, _ptr(Q), Q.stride(0), _ptr(QT), QT.stride(0), _ptr(row_scale),
+                                        _ptr(_f64(D, "D")), float(delta), _ptr(_f64(v, "v")), _ptr(_f64(out, "out"))))
     return out
 
 

@@ -85,3 +85,65 @@ def test_precision_form_with_a_large_sketch(nys):
     assert info["status"] in (0, 2), info
     rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, *(t.cpu().numpy() for t in (x, y, z)))
     assert rp <= tol and rd <= tol and mu <= tol
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def test_fp8_quantisation_matches_the_definition(nys):
+    """Per-row scales and E4M3 codes against the definition (FP32 division,
+    round to nearest even, saturation), bit for bit; the transposed copy
+    holds the same codes; padding is zero."""
+    m, n = 37, 53
+    rng = np.random.default_rng(8)
+    A = (rng.standard_normal((m, n)) * np.exp(rng.uniform(-6, 6, (m, 1)))).astype(np.float32)
+    A[4] = 0.0
+    A[7, 3] = 1e-30
+    h = nys.Handle(m, n, ell=4, precision_mode=2)
+    Q, QT, s = nys.nys_quantize_fp8(h, T(A))
+    Qref, sref = O.fp8_rowscale_quantize(A)
+    assert np.array_equal(s.cpu().numpy(), sref)
+    q = Q.cpu().numpy()
+    assert np.array_equal(O.e4m3_decode(q[:, :n]), Qref)
+    assert np.all(q[:, n:] == 0) and np.all(QT.cpu().numpy()[:, m:] == 0)
+    assert np.array_equal(QT.cpu().numpy()[:, :m], q[:, :n].T)
+
+
+@pytest.mark.parametrize("m,n", [(300, 1000), (1001, 4099)])
+def test_fp8_operator_matches_the_definition(nys, m, n):
+    """diag(s) Q (D .* (Q^T (s .* v))) + delta v with FP32 products and sums
+    against the same expression in FP64 on the decoded codes: FP32 rounding
+    of the inputs and of sums of up to max(m, n) terms."""
+    rng = np.random.default_rng(m + n)
+    A = (rng.standard_normal((m, n)) / np.sqrt(n)).astype(np.float32)
+    h = nys.Handle(m, n, ell=4, precision_mode=2)
+    Q, QT, s = nys.nys_quantize_fp8(h, T(A))
+    Qd = O.e4m3_decode(Q.cpu().numpy()[:, :n])
+    sv = s.cpu().numpy()
+    D = rng.uniform(0.1, 3.0, n)
+    v = rng.standard_normal(m)
+    out = nys.nys_normal_matvec_fp8(h, m, n, Q, QT, s, T(D), 1e-3, T(v)).cpu().numpy()
+    ref = O.fp8_normal_matvec(Qd, sv, D, 1e-3, v)
+    # elementwise bound: (max(m, n) + 4) * 2^-24 on the sums of |terms|
+    absref = np.abs(sv) * (np.abs(Qd) @ (D * (np.abs(Qd).T @ np.abs(sv * v)))) + 1e-3 * np.abs(v)
+    assert np.all(np.abs(out - ref) <= (max(m, n) + 4) * 2.0 ** -24 * absref * 2)
+
+
+def test_fp8_precision_form_meets_kkt(nys):
+    """precision_mode 2: FP8 inner PCG (E4M3 A and A^T with row scales),
+    FP32 float-float refinement: KKT <= 1e-6 on the FP32 problem, and the
+    solution agrees with the FP64 oracle's to the tolerance level."""
+    m, n, ell, tol = 600, 3000, 30, 1e-6
+    A32, A64, b, c, qp = _qp32(31, m, n)
+    ref = O.solve(A64, b, c, qp.q, qp.x0, qp.y0, qp.z0, O.Options(tol=tol, ell=ell, seed=5))
+    h = nys.Handle(m, n, ell=ell, tol=tol, seed=5, precision_mode=2)
+    x, y, z, info = nys.nys_solve(h, T(A32), T(b), T(c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    assert info["status"] in (0, 2), info
+    xs, ys, zs = (t.cpu().numpy() for t in (x, y, z))
+    rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, xs, ys, zs)
+    assert rp <= tol and rd <= tol and mu <= tol
+    err = np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x)
+    print(f"FP8 precision form: {info['ipm_iters']} IPM, {info['pcg_iters_total']} PCG, "
+          f"{info['refine_steps']} refinement steps; |x - x_oracle| / |x| = {err:.2e}")
+    assert err <= 1e-3

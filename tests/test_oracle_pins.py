@@ -346,3 +346,53 @@ def test_regularisation_trace_shape():
     rhos = [t.rho for t in r.trace]
     assert all(b <= a for a, b in zip(rhos, rhos[1:]))
     assert rhos[-1] < 1e-6
+
+
+# ---------------------------------------------------------------- FP8 storage
+
+def test_e4m3_rounding_follows_the_format_definition():
+    """E4M3 (sign, 4-bit exponent with bias 7, 3-bit mantissa, no infinities,
+    largest finite 1.75 * 2^8 = 448, subnormal spacing 2^-9): values worked
+    out from the definition, including ties to the even mantissa and
+    saturation."""
+    cases = {
+        448.0: 448.0, 500.0: 448.0, 1e6: 448.0, 1.0: 1.0,
+        1.0625: 1.0,            # halfway between 1.000 and 1.125: even mantissa 000
+        1.1875: 1.25,           # halfway between 1.125 and 1.250: even mantissa 010
+        -3.3: -3.25,            # spacing 0.25 in [2, 4)
+        2.0 ** -7: 2.0 ** -7,   # subnormal 4 * 2^-9
+        2.0 ** -10: 0.0,        # half a subnormal step: ties to 0
+        3 * 2.0 ** -10: 2.0 ** -8,  # 1.5 steps: ties to the even 2 steps
+        2.0 ** -6 * 1.0625: 2.0 ** -6,
+        240.0: 240.0, 248.0: 256.0,  # spacing 16 in [128, 256): 248 ties to even 256
+    }
+    got = O.e4m3_round(np.array(list(cases)))
+    assert np.array_equal(got, np.array(list(cases.values())))
+
+
+def test_e4m3_codes_decode_and_round_to_themselves():
+    """Every finite E4M3 code decodes to a value that rounds to itself;
+    the codes 0x7E, 0x08, 0x01 are 448, 2^-6 and 2^-9; 0x7F is NaN."""
+    vals = O.e4m3_decode(np.arange(256))
+    fin = np.isfinite(vals)
+    assert fin.sum() == 254                       # 0x7F and 0xFF are NaN
+    assert np.array_equal(O.e4m3_round(vals[fin]), vals[fin])
+    assert vals[0x7E] == 448.0 and vals[0x08] == 2.0 ** -6 and vals[0x01] == 2.0 ** -9
+    pos = np.sort(vals[1:0x7F])
+    assert np.all(np.diff(pos) > 0)               # 126 distinct positive values
+
+
+def test_fp8_rowscale_quantisation_bounds():
+    """Each nonzero row reaches +-448 after scaling; every element is within
+    half a quantum: |A - s Q| <= 2^-4 |A| in the normal range, <= s 2^-10
+    below it."""
+    rng = np.random.default_rng(3)
+    A = (rng.standard_normal((17, 40)) * np.exp(rng.uniform(-8, 8, (17, 1)))).astype(np.float32)
+    A[5] = 0.0
+    Q, s = O.fp8_rowscale_quantize(A)
+    assert s[5] == 1.0 and np.all(Q[5] == 0)
+    nz = np.arange(17) != 5
+    assert np.allclose(np.max(np.abs(Q[nz]), axis=1), 448.0)
+    err = np.abs(A.astype(np.float64) - s[:, None].astype(np.float64) * Q)
+    bound = np.maximum(2.0 ** -4 * np.abs(A), s[:, None] * 2.0 ** -10) * (1 + 1e-6)
+    assert np.all(err <= bound)
