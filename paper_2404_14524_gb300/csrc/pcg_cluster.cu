@@ -114,7 +114,7 @@ __device__ __forceinline__ void push_all(cg::cluster_group& cl, double* arr, int
 }
 
 template <bool kAS>
-__global__ void __launch_bounds__(kCT) k_pcg_cluster(ClusterPcgTask t0, const ClusterPcgTask* tasks) {
+__global__ void __launch_bounds__(kCT, kAS ? 1 : 3) k_pcg_cluster(ClusterPcgTask t0, const ClusterPcgTask* tasks) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -182,17 +182,34 @@ __global__ void __launch_bounds__(kCT) k_pcg_cluster(ClusterPcgTask t0, const Cl
   // partials of U^T r and ||r||^2 over own rows, pushed into every CTA
   auto ut_push = [&]() {
     __syncthreads();
-    for (int c = wid; c < ell; c += kCW) {
-      const double* u = Ub + (size_t)c * rb;
-      double a0 = 0.0, a1 = 0.0;
-      int ii = lane;
-      for (; ii + 32 < nr; ii += 64) {
-        a0 = fma(u[ii], Rb[ii], a0);
-        a1 = fma(u[ii + 32], Rb[ii + 32], a1);
+    if (row_warp) {
+      // short bands: a thread per column walks the band (few FP64
+      // instructions; a warp reduction per column would cost five)
+      for (int c = tid; c < ell; c += kCT) {
+        const double* u = Ub + (size_t)c * rb;
+        double a0 = 0.0, a1 = 0.0;
+        int ii = 0;
+        for (; ii + 1 < nr; ii += 2) {
+          a0 = fma(u[ii], Rb[ii], a0);
+          a1 = fma(u[ii + 1], Rb[ii + 1], a1);
+        }
+        if (ii < nr) a0 = fma(u[ii], Rb[ii], a0);
+        const double acc = a0 + a1;
+        for (int k = 0; k < C; ++k) *cl.map_shared_rank(UtIn + (size_t)rank * (ell + 1) + c, k) = acc;
       }
-      if (ii < nr) a0 = fma(u[ii], Rb[ii], a0);
-      const double acc = warp_sum(a0 + a1);
-      push_all(cl, UtIn + (size_t)rank * (ell + 1), c, acc, C, lane);
+    } else {
+      for (int c = wid; c < ell; c += kCW) {
+        const double* u = Ub + (size_t)c * rb;
+        double a0 = 0.0, a1 = 0.0;
+        int ii = lane;
+        for (; ii + 32 < nr; ii += 64) {
+          a0 = fma(u[ii], Rb[ii], a0);
+          a1 = fma(u[ii + 32], Rb[ii + 32], a1);
+        }
+        if (ii < nr) a0 = fma(u[ii], Rb[ii], a0);
+        const double acc = warp_sum(a0 + a1);
+        push_all(cl, UtIn + (size_t)rank * (ell + 1), c, acc, C, lane);
+      }
     }
     double v = 0.0;
     if (row_thread)
@@ -251,40 +268,59 @@ __global__ void __launch_bounds__(kCT) k_pcg_cluster(ClusterPcgTask t0, const Cl
     // p = z + beta p (all rows)
     for (int i = tid; i < m; i += kCT) P[i] = it == 0 ? Zf[i] : fma(beta, P[i], Zf[i]);
     __syncthreads();
-    // t = D .* (A^T p) over own columns: lanes over 4 x 32 columns, warps over
-    // rows (two interleaved accumulators each), then a tree over the warps
+    // t = D .* (A^T p) over own columns: lanes over 32 columns, warps over
+    // rows (two interleaved accumulators each), then a tree over the warps.
+    // One 32-column block at a time: a warp-uniform loop, so no FP64
+    // instruction is issued for columns beyond the band (a predicated-off
+    // FP64 instruction costs a full warp slot on this GPU).
     for (int c0 = 0; c0 < nc; c0 += kChunk) {
-      double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
-      int i = wid;
-      for (; i + kCW < m; i += 2 * kCW) {
-        const double p0 = P[i], p1 = P[i + kCW];
+      const int nb = min(kChunk, nc - c0);
+      if (!kAS && nb == kChunk) {
+        // A from L2: four 32-column blocks per pass over the rows (longer
+        // contiguous reads per row); every block is inside the band
+        double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+        int i = wid;
+        for (; i + kCW < m; i += 2 * kCW) {
+          const double p0 = P[i], p1 = P[i + kCW];
+          const double* r0p = T.A + (long long)i * T.lda + j0 + c0 + lane;
+          const double* r1p = T.A + (long long)(i + kCW) * T.lda + j0 + c0 + lane;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int jj = c0 + u * 32 + lane;
-          if (jj < nc) {
+          for (int u = 0; u < 4; ++u) {
+            a[u] = fma(__ldg(r0p + u * 32), p0, a[u]);
+            b[u] = fma(__ldg(r1p + u * 32), p1, b[u]);
+          }
+        }
+        if (i < m) {
+          const double p0 = P[i];
+          const double* r0p = T.A + (long long)i * T.lda + j0 + c0 + lane;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = fma(__ldg(r0p + u * 32), p0, a[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) red[wid * kChunk + u * 32 + lane] = a[u] + b[u];
+      } else
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int jj = c0 + b0 + lane;
+        const bool on = b0 + lane < nb;
+        double a = 0.0, b = 0.0;
+        if (on) {
+          int i = wid;
+          for (; i + kCW < m; i += 2 * kCW) {
             const double x0 = kAS ? As[(size_t)i * L.ncp + jj] : __ldg(T.A + (long long)i * T.lda + j0 + jj);
             const double x1 = kAS ? As[(size_t)(i + kCW) * L.ncp + jj]
                                   : __ldg(T.A + (long long)(i + kCW) * T.lda + j0 + jj);
-            a[u] = fma(x0, p0, a[u]);
-            b[u] = fma(x1, p1, b[u]);
+            a = fma(x0, P[i], a);
+            b = fma(x1, P[i + kCW], b);
           }
-        }
-      }
-      if (i < m) {
-        const double p0 = P[i];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int jj = c0 + u * 32 + lane;
-          if (jj < nc) {
+          if (i < m) {
             const double x0 = kAS ? As[(size_t)i * L.ncp + jj] : __ldg(T.A + (long long)i * T.lda + j0 + jj);
-            a[u] = fma(x0, p0, a[u]);
+            a = fma(x0, P[i], a);
           }
         }
+        red[wid * kChunk + b0 + lane] = a + b;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) red[wid * kChunk + u * 32 + lane] = a[u] + b[u];
       __syncthreads();
-      for (int c = tid; c < kChunk && c0 + c < nc; c += kCT) {
+      for (int c = tid; c < nb; c += kCT) {
         double w8[kCW];
 #pragma unroll
         for (int w = 0; w < kCW; ++w) w8[w] = red[w * kChunk + c];

@@ -140,35 +140,25 @@ __global__ void __launch_bounds__(kPT) k_pcg_persistent(int m, int n, const doub
     // warps over rows (two interleaved accumulators each), lanes over 64
     // columns, then a fixed tree over the warps: no thread walks a whole
     // column, so the FP64 latency chains stay short
-    for (int c0 = j0; c0 < j1; c0 += 64) {
-      double a[2] = {0.0, 0.0}, b[2] = {0.0, 0.0};
-      int i = wid;
-      for (; i + kPW < m; i += 2 * kPW) {
-        const double p0 = ps[i], p1 = ps[i + kPW];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int j = c0 + u * 32 + lane;
-          if (j < j1) {
-            a[u] = fma(__ldg(A + (long long)i * lda + j), p0, a[u]);
-            b[u] = fma(__ldg(A + (long long)(i + kPW) * lda + j), p1, b[u]);
-          }
+    for (int c0 = j0; c0 < j1; c0 += 32) {
+      // one 32-column block at a time (warp-uniform loop: no predicated-off
+      // FP64 instructions for columns past the band)
+      const int j = c0 + lane;
+      double a = 0.0, b = 0.0;
+      if (j < j1) {
+        int i = wid;
+        for (; i + kPW < m; i += 2 * kPW) {
+          a = fma(__ldg(A + (long long)i * lda + j), ps[i], a);
+          b = fma(__ldg(A + (long long)(i + kPW) * lda + j), ps[i + kPW], b);
         }
+        if (i < m) a = fma(__ldg(A + (long long)i * lda + j), ps[i], a);
       }
-      if (i < m) {
-        const double p0 = ps[i];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int j = c0 + u * 32 + lane;
-          if (j < j1) a[u] = fma(__ldg(A + (long long)i * lda + j), p0, a[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) red[wid * 64 + u * 32 + lane] = a[u] + b[u];
+      red[wid * 32 + lane] = a + b;
       __syncthreads();
-      if (tid < 64 && c0 + tid < j1) {
+      if (tid < 32 && c0 + tid < j1) {
         double w8[kPW];
 #pragma unroll
-        for (int w = 0; w < kPW; ++w) w8[w] = red[w * 64 + tid];
+        for (int w = 0; w < kPW; ++w) w8[w] = red[w * 32 + tid];
 #pragma unroll
         for (int st = 1; st < kPW; st <<= 1)
 #pragma unroll
