@@ -242,6 +242,25 @@ __device__ __forceinline__ void jacobi_rotation(double al, double be, double ga,
   }
 }
 
+// Sums of three values over a warp in six FP64 additions instead of fifteen
+// (a warp-wide FP64 instruction costs a full pipe slot however few lanes
+// it uses): the first two exchange levels give each lane one quantity, the
+// last three finish it within groups of eight lanes.  On return lanes 0-7
+// hold the sum of a, 8-15 that of b, 16-23 that of c.  Whole warp only.
+__device__ __forceinline__ double warp_sum3(double a, double b, double c) {
+  const int lane = threadIdx.x & 31;
+  const bool lo = lane < 16;
+  const double r1 = __shfl_xor_sync(0xffffffffu, lo ? c : a, 16);
+  const double r2 = __shfl_xor_sync(0xffffffffu, lo ? 0.0 : b, 16);
+  const double x = (lo ? a : c) + r1;
+  const double y = (lo ? b : 0.0) + r2;
+  const bool b3 = (lane & 8) != 0;
+  double v = (b3 ? y : x) + __shfl_xor_sync(0xffffffffu, b3 ? x : y, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void __launch_bounds__(kNT) k_jacobi(int m, int ell, double* B, int ld, double tol,
                                                 int* sweep_flags, int max_sweeps, unsigned* bar,
                                                 int* err, int* sweeps_out) {
@@ -347,9 +366,12 @@ __global__ void __launch_bounds__(kJT) k_jacobi_smem(int m, int ell, double* B, 
           be = fma(y, y, be);
           ga = fma(x, y, ga);
         }
-        al = warp_sum(al + al2);
-        be = warp_sum(be + be2);
-        ga = warp_sum(ga + ga2);
+        {
+          const double v = warp_sum3(al + al2, be + be2, ga + ga2);
+          al = __shfl_sync(0xffffffffu, v, 0);
+          be = __shfl_sync(0xffffffffu, v, 8);
+          ga = __shfl_sync(0xffffffffu, v, 16);
+        }
         if (jacobi_needs_rotation(al, be, ga, tol)) {
           double c, sn;
           jacobi_rotation(al, be, ga, c, sn);
@@ -386,6 +408,7 @@ __global__ void __launch_bounds__(kJT) k_jacobi_smem(int m, int ell, double* B, 
 // k_jacobi.
 constexpr int kJC = 256;
 constexpr int kJCW = kJC / 32;
+constexpr int kJDW = 4;                  // warps that form the inner products
 constexpr int kJacobiClusterMaxEll = 32;
 constexpr int kJacobiClusterMaxRows = 6144;   // 4 columns of m doubles per CTA: 192 KB
 
@@ -439,25 +462,30 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
       if (q < ell) {
         double* bp = col(cur, 0);
         double* bq = col(cur, 1);
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int i = tid; i < m; i += kJC) {
-          const double x = bp[i], y = bq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
+        // the three inner products over the rows: four warps (one per
+        // sub-partition), packed warp sums, then lane 0 of warp 0 combines
+        if (wid < kJDW) {
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int i = tid; i < m; i += 32 * kJDW) {
+            const double x = bp[i], y = bq[i];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+          const double v = warp_sum3(al, be, ga);
+          if (lane == 0) red[wid] = v;
+          else if (lane == 8) red[kJCW + wid] = v;
+          else if (lane == 16) red[2 * kJCW + wid] = v;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (lane == 0) { red[wid] = al; red[kJCW + wid] = be; red[2 * kJCW + wid] = ga; }
         __syncthreads();
         if (wid == 0) {
-          double a = lane < kJCW ? red[lane] : 0.0;
-          double b = lane < kJCW ? red[kJCW + lane] : 0.0;
-          double g = lane < kJCW ? red[2 * kJCW + lane] : 0.0;
-          a = warp_sum(a);
-          b = warp_sum(b);
-          g = warp_sum(g);
+          const int q8 = lane >> 3, r8 = lane & 7;
+          double v = (q8 < 3 && r8 < kJDW) ? red[q8 * kJCW + r8] : 0.0;
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          const double a = v;
+          const double b = __shfl_sync(0xffffffffu, v, 8);
+          const double g = __shfl_sync(0xffffffffu, v, 16);
           if (lane == 0) {
             if (jacobi_needs_rotation(a, b, g, tol)) {
               double c, sn;
