@@ -95,6 +95,19 @@ __device__ __forceinline__ double tree_sum(const double* v, int C, size_t stride
   return a[0];
 }
 
+// Partial sum of the values k in [4w, 4w + 4) (those below C) of a strided
+// array, as ((v0 + v1) + (v2 + v3)): four warps each take one quarter, and
+// (g0 + g1) + (g2 + g3) then reproduces tree_sum's order exactly.
+__device__ __forceinline__ double quad_sum(const double* v, int C, size_t stride, int w) {
+  double a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int idx = 4 * w + k;
+    a[k] = idx < C ? v[(size_t)idx * stride] : 0.0;
+  }
+  return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
 // Sum of C (<= 16) values with one per lane (a fixed xor tree of four
 // levels), broadcast from lane 0; called by a whole warp.
 __device__ __forceinline__ double lane_sum(const double* v, int C, int lane) {
@@ -219,10 +232,22 @@ __global__ void __launch_bounds__(kCT, kAS ? 1 : 3) k_pcg_cluster(ClusterPcgTask
   };
   // s = U^T r (into wss as ws .* s) and ||r||^2 (returned) from the pushed partials
   auto ut_gather = [&]() -> double {
-    for (int e = tid; e <= ell; e += kCT) {
-      const double s = tree_sum(UtIn + e, C, (size_t)(ell + 1));
-      if (e < ell) wss[e] = ws[e] * s;
-      else bc[0] = s;
+    if (4 * (ell + 1) <= kCW * kChunk) {
+      // four warps (one per sub-partition) each add a quarter of the partials
+      if (wid < 4)
+        for (int e = lane; e <= ell; e += 32) red[wid * (ell + 1) + e] = quad_sum(UtIn + e, C, (size_t)(ell + 1), wid);
+      __syncthreads();
+      for (int e = tid; e <= ell; e += kCT) {
+        const double s = (red[e] + red[(ell + 1) + e]) + (red[2 * (ell + 1) + e] + red[3 * (ell + 1) + e]);
+        if (e < ell) wss[e] = ws[e] * s;
+        else bc[0] = s;
+      }
+    } else {
+      for (int e = tid; e <= ell; e += kCT) {
+        const double s = tree_sum(UtIn + e, C, (size_t)(ell + 1));
+        if (e < ell) wss[e] = ws[e] * s;
+        else bc[0] = s;
+      }
     }
     __syncthreads();
     return bc[0];
@@ -230,7 +255,28 @@ __global__ void __launch_bounds__(kCT, kAS ? 1 : 3) k_pcg_cluster(ClusterPcgTask
   // z = r + U (ws .* s) on own rows, pushed into every CTA's Zf; partial r^T z pushed
   auto z_push = [&]() {
     double v = 0.0;
-    if (row_thread) {
+    if (row_warp) {
+      // columns of U in four quarters, one per warp (sub-partition), then warp
+      // 0 adds the quarters for its rows
+      const int cq = (ell + 3) / 4;
+      if (wid < 4 && lane < nr) {
+        const int c0 = wid * cq, c1 = min(ell, c0 + cq);
+        double a0 = 0.0, a1 = 0.0;
+        int c = c0;
+        for (; c + 1 < c1; c += 2) {
+          a0 = fma(Ub[(size_t)c * rb + lane], wss[c], a0);
+          a1 = fma(Ub[(size_t)(c + 1) * rb + lane], wss[c + 1], a1);
+        }
+        if (c < c1) a0 = fma(Ub[(size_t)c * rb + lane], wss[c], a0);
+        red[wid * 32 + lane] = a0 + a1;
+      }
+      __syncthreads();
+      if (wid == 0 && lane < nr) {
+        const double zi = Rb[lane] + ((red[lane] + red[32 + lane]) + (red[64 + lane] + red[96 + lane]));
+        for (int k = 0; k < C; ++k) *cl.map_shared_rank(Zf + i0 + lane, k) = zi;
+        v = Rb[lane] * zi;
+      }
+    } else if (row_thread) {
       for (int ii = tid; ii < nr; ii += row_stride) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int c = 0;
@@ -367,7 +413,17 @@ __global__ void __launch_bounds__(kCT, kAS ? 1 : 3) k_pcg_cluster(ClusterPcgTask
     // w = delta p + sum_k q_k on own rows; partial p^T w pushed
     {
       double v = 0.0;
-      if (row_thread) {
+      if (row_warp) {
+        // four warps each add a quarter of the C partials of the band's rows
+        if (wid < 4 && lane < nr) red[wid * 32 + lane] = quad_sum(Qin + lane, C, (size_t)rb, wid);
+        __syncthreads();
+        if (wid == 0 && lane < nr) {
+          const double s = (red[lane] + red[32 + lane]) + (red[64 + lane] + red[96 + lane]);
+          const double wi = fma(delta, P[i0 + lane], s);
+          Wb[lane] = wi;
+          v = P[i0 + lane] * wi;
+        }
+      } else {
         for (int ii = tid; ii < nr; ii += row_stride) {
           const double wi = fma(delta, P[i0 + ii], tree_sum(Qin + ii, C, (size_t)rb));
           Wb[ii] = wi;
