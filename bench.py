@@ -163,9 +163,18 @@ def host_workload(w, rank):
     return None
 
 
-def device_workload(w, rank, dev):
+def device_workload(w, rank, dev, host_gen=False):
     from paper_2404_14524_gb300 import synth
     import torch
+    if host_gen:
+        # the same spectrum generated with numpy (no device QR), FP32 A the problem
+        qp = synth.spectral_qp(1237 + 1000 * rank, w["m"], w["n"], "exp200", "uniform")
+        A32 = qp.A.astype(np.float32)
+        A64 = A32.astype(np.float64)
+        b = A64 @ qp.x0
+        c = A64.T @ qp.y0 + qp.z0 - qp.q * qp.x0
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        return (T(A32), T(b), T(c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
     A, b, c, q, x0, y0, z0 = synth.spectral_qp_device(1237 + 1000 * rank, w["m"], w["n"], "exp200", "uniform",
                                                       device=dev, dtype=torch.float32)
     torch.cuda.synchronize(dev)
@@ -267,6 +276,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-gen", action="store_true",
+                    help="generate the large precision workloads with numpy instead of on the GPU")
     ap.add_argument("--no-gemv", action="store_true",
                     help="skip the operator GEMV measurement at the large workload shapes")
     ap.add_argument("--compare-fp64", action="store_true",
@@ -313,7 +324,7 @@ def main():
             ell = min(w["ell"], max(1, qp.m // 4)) if form == "batch" else w["ell"]
             dev_probs.append(tuple(T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0)) + (ell,))
     else:
-        dev_probs = [device_workload(w, rank, dev) + (w["ell"],)]
+        dev_probs = [device_workload(w, rank, dev, args.host_gen) + (w["ell"],)]
     mmax = max(p[0].shape[0] for p in dev_probs)
     nmax = max(p[0].shape[1] for p in dev_probs)
     a_bytes = sum(p[0].numel() * p[0].element_size() for p in dev_probs)

@@ -223,23 +223,33 @@ __device__ __forceinline__ bool jacobi_needs_rotation(double al, double be, doub
 
 // Rotation (c, s) that zeroes the inner product (Rutishauser's formulas):
 // zeta = (be - al) / (2 ga), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-// c = 1 / sqrt(1 + t^2), s = c t.  For |zeta| > 2^13 the first-order angle
-// t = ga / (be - al) is used with c = 1 - t^2 / 2, which is orthogonal to
-// double precision (c^2 (1 + t^2) = 1 - O(t^4), t^4 < 2^-56); the small angle
-// error only leaves a residual inner product of relative size 1/(4 zeta^2)
-// for the next sweep.  One division instead of three divisions and two roots.
+// c = 1 / sqrt(1 + t^2), s = c t.  Written as t = 2 ga sign(d) /
+// (|d| + sqrt(d^2 + 4 ga^2)) with d = be - al (the same number, one root and
+// one division instead of two of each; sign(0) = +1 reproduces the sign that
+// zeta = +-0 gives) and c from a reciprocal square root.  For |zeta| > 2^13
+// the first-order angle t = ga / d with c = 1 - t^2 / 2 is used, which is
+// orthogonal to double precision (c^2 (1 + t^2) = 1 - O(t^4), t^4 < 2^-56);
+// its angle error leaves a residual inner product of relative size
+// 1/(4 zeta^2) for the next sweep.  FP64 divisions and roots cost hundreds of
+// cycles of latency each on this GPU, and a round waits for this chain.
 __device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double& c, double& s) {
   const double d = be - al;
   if (fabs(d) > 16384.0 * fabs(ga)) {
     const double t = ga / d;
     c = fma(-0.5 * t, t, 1.0);
     s = c * t;
-  } else {
-    const double zeta = d / (2.0 * ga);
-    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-    c = 1.0 / sqrt(fma(t, t, 1.0));
-    s = c * t;
+    return;
   }
+  const double h = fma(d, d, 4.0 * ga * ga);
+  double t;
+  if (isfinite(h)) {
+    t = (2.0 * ga) * copysign(1.0, d == 0.0 ? 1.0 : d) / (fabs(d) + sqrt(h));
+  } else {                       // squares out of range: the zeta form
+    const double zeta = d / (2.0 * ga);
+    t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+  }
+  c = rsqrt(fma(t, t, 1.0));
+  s = c * t;
 }
 
 // Sums of three values over a warp in six FP64 additions instead of fifteen
