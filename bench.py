@@ -282,7 +282,7 @@ def main():
                     help="skip the operator GEMV measurement at the large workload shapes")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision workloads: also time one FP64-form solve of the same QP")
-    ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm"],
+    ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm", "ff_pcg", "bf16_pcg"],
                     help="run only this kernel --reps times on an m x n (x ell) case (for ncu captures)")
     ap.add_argument("--m", type=int, default=5000)
     ap.add_argument("--n", type=int, default=20000)
@@ -529,6 +529,21 @@ def profile_kernel(args):
         v = torch.randn(m, generator=g, device=dev, dtype=torch.float64)
         run = lambda: nys.nys_normal_matvec_lp(h, A, AT, D, 1e-3, v)
         work = {"bytes": 4.0 * m * n, "flops": 4.0 * m * n}
+    elif args.profile_kernel in ("ff_pcg", "bf16_pcg"):
+        # forced PCG iterations on the precision form's operator (graph route)
+        ell = min(args.ell, 64)
+        A32 = torch.randn(m, n, generator=g, device=dev) / n ** 0.5
+        h = nys.Handle(m, n, ell=ell, precision_mode=1)
+        D = torch.rand(n, generator=g, device=dev, dtype=torch.float64) + 0.5
+        U = torch.zeros(ell, m, device=dev, dtype=torch.float64)     # orthonormal columns e_0 .. e_{ell-1}
+        U[torch.arange(ell, device=dev), torch.arange(ell, device=dev)] = 1.0
+        lam = torch.linspace(10.0, 1.0, ell, device=dev, dtype=torch.float64)
+        xi = torch.randn(m, generator=g, device=dev, dtype=torch.float64)
+        opk = "ff" if args.profile_kernel == "ff_pcg" else "bf16"
+        iters = 40
+        run = lambda: nys.nys_pcg_lp(h, A32, opk, D, 1e-3, U, lam, xi, 0.0, iters, forced=iters)
+        per = 8.0 if opk == "ff" else 4.0
+        work = {"bytes": per * m * n * iters, "flops": 4.0 * m * n * iters}
     else:
         ell = args.ell
         A = (torch.randn(m, n, generator=g, device=dev) / 100).to(torch.bfloat16)

@@ -270,6 +270,19 @@ int nys_pcg(nys_handle h, int m, int n, int a_dtype, const void* A, long long ld
             const double* xi, double* dy, double eta, int max_iter, int forced_iters,
             int* iters, double* res_norm);
 
+/* The same PCG on the precision form's operators (the inner solves of
+ * precision_mode 1 and 2 and their final stage): the FP32 matrix A (device,
+ * m x n, lda) is first copied into the handle's operator storage, then
+ * (N_r + delta I) dy = xi is solved with N_r = A_r diag(D) A_r^T for
+ * op_dtype NYS_BF16 (BF16 copies, FP32 sums), NYS_FP8E4M3 (E4M3 copies with
+ * per-row scales, FP32 sums; precision_mode 2 handles only) or NYS_F32 (the
+ * FP32 matrix with float-float sums, the problem's own operator).  Vectors
+ * FP64; other arguments and results as nys_pcg.  The handle must be a
+ * precision-form handle. */
+int nys_pcg_lp(nys_handle h, int m, int n, const float* A, long long lda, int op_dtype, const double* D,
+               double delta, int ell, const double* U, int ld, const double* lam, const double* xi, double* dy,
+               double eta, int max_iter, int forced_iters, int* iters, double* res_norm);
+
 /* Which implementation nys_pcg / nys_solve use for an FP64 system of this
  * size (the same arithmetic in each; they differ only in summation order):
  *   NYS_ROUTE_CLUSTER_SMEM  one thread-block cluster, A's column bands in

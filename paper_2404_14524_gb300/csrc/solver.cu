@@ -1376,6 +1376,35 @@ int nys_pcg(nys_handle h, int m, int n, int a_dtype, const void* A, long long ld
   return rc;
 }
 
+int nys_pcg_lp(nys_handle h, int m, int n, const float* A, long long lda, int op_dtype, const double* D,
+               double delta, int ell, const double* U, int ld, const double* lam, const double* xi, double* dy,
+               double eta, int max_iter, int forced_iters, int* iters, double* res_norm) {
+  if (!h) return NYS_ERR_ARG;
+  if (!h->lp_arena) return fail(h, NYS_ERR_ARG, "nys_pcg_lp: not a precision-form handle");
+  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || lda < n || ell <= 0 || ell > h->ell_cap || ld < m ||
+      !A || !D || !U || !lam || !xi || !dy || !iters || !res_norm || max_iter < 0 || dy == xi ||
+      (op_dtype != NYS_BF16 && op_dtype != NYS_F32 && op_dtype != NYS_FP8E4M3) ||
+      (op_dtype == NYS_FP8E4M3 && !h->rs64))
+    return fail(h, NYS_ERR_ARG, "nys_pcg_lp: bad argument");
+  CK(cudaMemsetAsync(h->si + SI_ERR, 0, sizeof(int), h->st));
+  Prob P{m, n, 1, nullptr, A, lda};
+  if (op_dtype == NYS_BF16)
+    CK(convert_transpose(h->st, m, n, 0, A, lda, h->Ab, h->ld_b, h->AbT, h->ld_bt, nullptr, 0));
+  else if (op_dtype == NYS_F32)
+    CK(convert_transpose(h->st, m, n, 0, A, lda, nullptr, 0, nullptr, 0, h->AfT, h->ld_ft));
+  else
+    CK(quantize_fp8(h->st, m, n, A, lda, h->rs32, h->rs64, h->A8, h->ld_q, h->A8T, h->ld_qt));
+  CK(to_f32(h->st, n, (int)align_up(n, 8), D, nullptr, h->Df));
+  OpSpec op{};
+  op.kind = op_dtype == NYS_BF16 ? 1 : op_dtype == NYS_F32 ? 3 : 4;
+  op.lp = make_lp_op(h, P, op.kind, D);
+  int rc = run_pcg(h, m, n, op, delta, ell, U, ld, lam, xi, dy, eta, max_iter, forced_iters, iters);
+  CK(cudaMemcpyAsync(h->h_red, h->sd, sizeof(double) * SD_COUNT, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  *res_norm = std::sqrt(h->h_red[SD_RR]);
+  return rc;
+}
+
 int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda, const double* x,
                const double* z, const double* D, double delta, const double* r_d, const double* r_p,
                const double* r_xz, int ell, const double* U, int ld, const double* lam, double eta,

@@ -96,6 +96,8 @@ _SIGS = {
     "nys_precond_apply": (_I, [_P, _I, _I, _P, _I, _P, _D, _P, _P]),
     "nys_pcg": (_I, [_P, _I, _I, _I, _P, _LL, _P, _D, _I, _P, _I, _P, _P, _P, _D, _I, _I,
                      ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "nys_pcg_lp": (_I, [_P, _I, _I, _P, _LL, _I, _P, _D, _I, _P, _I, _P, _P, _P, _D, _I, _I,
+                        ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "nys_newton": (_I, [_P, _I, _I, _I, _P, _LL, _P, _P, _P, _D, _P, _P, _P, _I, _P, _I, _P, _D,
                         _I, _I, _P, _P, _P, ctypes.POINTER(_I)]),
     "nys_step_length": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
@@ -329,6 +331,28 @@ def nys_pcg(h: Handle, A, D, delta: float, U, lam, xi, eta: float, max_iter: int
                        _ptr(_f64(xi, "xi")), _ptr(_f64(out, "dy")), float(eta), int(max_iter),
                        int(forced), ctypes.byref(it), ctypes.byref(res))
     h.check(rc)
+    return out, it.value, res.value, rc
+
+
+def nys_pcg_lp(h: Handle, A32, op: str, D, delta: float, U, lam, xi, eta: float, max_iter: int, forced: int = -1,
+               out=None):
+    """PCG on the precision form's operator built from the FP32 matrix A32:
+    op "bf16", "fp8" or "ff" (FP32 with float-float sums).  Returns
+    (dy, iters, |r|, status)."""
+    m, n = A32.shape
+    ell = U.shape[0]
+    dt = {"bf16": NYS_BF16, "fp8": NYS_FP8E4M3, "ff": NYS_F32}[op]
+    out = torch.empty_like(xi) if out is None else out
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    if A32.dtype != torch.float32 or A32.stride(1) != 1:
+        raise TypeError("A must be row-major float32")
+    rc = lib().nys_pcg_lp(h.h, m, n, _ptr(A32), A32.stride(0), dt, _ptr(_f64(D, "D")), float(delta), ell,
+                          _ptr(_f64(U, "U")), U.shape[1], _ptr(_f64(lam, "lam")), _ptr(_f64(xi, "xi")),
+                          _ptr(_f64(out, "out")),
+                          float(eta), int(max_iter), int(forced), ctypes.byref(it), ctypes.byref(res))
+    if rc < 0:
+        h.check(rc)
     return out, it.value, res.value, rc
 
 

@@ -147,3 +147,36 @@ def test_fp8_precision_form_meets_kkt(nys):
     print(f"FP8 precision form: {info['ipm_iters']} IPM, {info['pcg_iters_total']} PCG, "
           f"{info['refine_steps']} refinement steps; |x - x_oracle| / |x| = {err:.2e}")
     assert err <= 1e-3
+
+
+@pytest.mark.parametrize("op", ["ff", "bf16", "fp8"])
+def test_precision_operator_pcg(nys, op):
+    """PCG on the precision form's operators: with the float-float FP32
+    operator it solves the FP32 matrix's system (true FP64 residual at the
+    tolerance); with BF16 / FP8 storage it solves the system of the rounded
+    matrix (residual measured with the rounded values)."""
+    m, n, ell = 400, 1600, 16
+    rng = np.random.default_rng(12)
+    A32 = (rng.standard_normal((m, n)) * (np.arange(1, m + 1) ** -0.5)[:, None] / np.sqrt(n)).astype(np.float32)
+    A64 = A32.astype(np.float64)
+    D = rng.uniform(0.1, 3.0, n)
+    Om = O.gaussian_omega(3, 0, m, ell)
+    F = O.nystrom_from_sketch(O.sketch(A64, D, Om), Om)
+    xi = rng.standard_normal(m)
+    delta, eta = 1e-3, 1e-8
+    h = nys.Handle(m, n, ell=ell, precision_mode=2 if op == "fp8" else 1)
+    U = T(np.ascontiguousarray(F.U.T))
+    dy, it, res, rc = nys.nys_pcg_lp(h, T(A32), op, T(D), delta, U, T(F.lam), T(xi), eta, 2000)
+    assert rc == 0 and it < 2000
+    y = dy.cpu().numpy()
+    if op == "ff":
+        Ar = A64
+    elif op == "bf16":
+        Ar = torch.from_numpy(A32).to(torch.bfloat16).double().numpy()
+    else:
+        Q, s = O.fp8_rowscale_quantize(A32)
+        Ar = s[:, None].astype(np.float64) * Q
+    r = np.linalg.norm(xi - O.normal_matvec(Ar, D, delta, y)) / np.linalg.norm(xi)
+    # FP32 products: the recursive residual meets eta; the true one within the
+    # operator's rounding (n 2^-24 relative for the FP32 sums, 2^-44 for float-float)
+    assert r <= (10 * eta if op == "ff" else 10 * eta + 1e-5)
