@@ -11,11 +11,17 @@ of the paper, step by step and in the paper's notation, with library routines
 Readings taken where the paper is silent or garbled are marked READING.
 
 Scope: the practical method (Algorithm 6 driving the Mehrotra predictor-corrector
-of Algorithm 5 and the Newton solve of Algorithm 4) restricted to the
-all-non-negative case I = {1..n}, F = J = {} of problem (P)/(D).
+of Algorithm 5 and the Newton solve of Algorithm 4) for problem (P)/(D), where
+every variable is non-negative (I = {1..n}), and for its generalisation
+(P~)/(D~) with free variables (set F) and box-constrained variables
+0 <= x_j <= u_j (set J) of the section on free and box-constrained variables.
+The all-non-negative case is the general code with F = J = {}: it only adds
+exact zeros, so both cases share one implementation.
 
 Pinning (tests/test_oracle_*.py): every function is checked against something
-other than itself -- the assembled 3x3-block Newton system (Eq. Newton),
+other than itself -- the assembled 3x3-block Newton system (Eq. Newton) and
+the 5x5-block system with free and box-constrained variables
+(Eq. Newton-free-box), scipy's HiGHS on bounded LPs,
 P_Nys from Eq. Nys_precond against P_Nys^{-1} from Eq. Nys_precond_inv, the
 Nystrom invariants of Section 2.3.2, a dense direct solve of the normal
 equations, brute-force active-set solutions of tiny QPs, hand-derived KKT
@@ -85,10 +91,27 @@ def eps_of(x: float) -> float:
 # Normal-equations operator (Section 2.1.2, Eq. normal-eq).
 # ---------------------------------------------------------------------------
 
-def scaling_D(x: np.ndarray, z: np.ndarray, q: np.ndarray, rho: float) -> np.ndarray:
+# Variable kinds of (P~)/(D~): x_j >= 0 (I), free (F), 0 <= x_j <= u_j (J).
+KIND_I, KIND_F, KIND_J = 0, 1, 2
+
+
+def scaling_D(x: np.ndarray, z: np.ndarray, q: np.ndarray, rho: float,
+              kind: np.ndarray | None = None, w: np.ndarray | None = None,
+              s: np.ndarray | None = None) -> np.ndarray:
     """Diagonal of (Q + Theta^{-1} + rho I)^{-1} with Theta = X Z^{-1}
-    (Section 2.1.2, below Eq. delta_z)."""
-    return 1.0 / (q + z / x + rho)
+    (Section 2.1.2, below Eq. delta_z).
+
+    With free and box-constrained variables (Eq. normal-eq-free-box),
+    eliminating dz, dw and ds from Eq. Newton-free-box leaves
+    Theta^{-1}_j = z_j / x_j on I, z_j / x_j + s_j / w_j on J and 0 on F."""
+    if kind is None:
+        return 1.0 / (q + z / x + rho)
+    theta_inv = np.zeros_like(x)
+    ij = kind != KIND_F
+    theta_inv[ij] = z[ij] / x[ij]
+    jj = kind == KIND_J
+    theta_inv[jj] += s[jj] / w[jj]
+    return 1.0 / (q + theta_inv + rho)
 
 
 def normal_matvec(A: np.ndarray, D: np.ndarray, delta: float, v: np.ndarray) -> np.ndarray:
@@ -262,26 +285,51 @@ class Direction:
     dz: np.ndarray
     pcg_iters: int
     pcg_res: float
+    dw: np.ndarray | None = None      # box-constrained variables only
+    ds: np.ndarray | None = None
 
 
 def newton_direction(A, x, z, D, delta, r_d, r_p, r_xz, F, eta, maxit,
-                     forced_iters=None) -> Direction:
-    """Algorithm 4 for I = {1..n}:
+                     forced_iters=None, kind=None, w=None, s=None, r_u=None,
+                     r_ws=None) -> Direction:
+    """Algorithm 4.  For I = {1..n} (kind None):
     xi_au = -X^{-1} r_xz;  xi = r_p + A D (r_d + xi_au);
     (A D A^T + delta I) dy = xi by Nystrom PCG;
     dx = D (A^T dy - r_d - xi_au);
     dz = X^{-1} (r_xz - Z dx).
-    READING: Algorithm 4 prints dz = X^{-1} r_xz - Z dx; Eq. delta_z and the
-    third block row of Eq. Newton give X^{-1}(r_xz - Z dx), which is used."""
-    xi_au = -r_xz / x
+    With free (F) and box-constrained (J) variables, `kind` marks each index
+    and w, s, r_u, r_ws are the slack, its dual and their right-hand sides
+    (zero outside J):
+    xi_au = 0 on F, -r_xz / x on I, -r_xz / x + r_ws / w - s r_u / w on J;
+    dw = r_u - dx on J (0 elsewhere); dz = X^{-1}(r_xz - Z dx) on I and J
+    (0 on F); ds = W^{-1}(r_ws - S dw) on J (0 elsewhere).
+    READING: Algorithm 4 prints dz = X^{-1} r_xz - Z dx (and ds = W^{-1} r_ws
+    - S dw); the corresponding block rows of Eq. Newton / Eq. Newton-free-box
+    give X^{-1}(r_xz - Z dx) and W^{-1}(r_ws - S dw), which are used."""
+    if kind is None:
+        xi_au = -r_xz / x
+    else:
+        xi_au = np.zeros_like(x)
+        ij = kind != KIND_F
+        jj = kind == KIND_J
+        xi_au[ij] = -r_xz[ij] / x[ij]
+        xi_au[jj] += r_ws[jj] / w[jj] - s[jj] * r_u[jj] / w[jj]
     xi = r_p + A @ (D * (r_d + xi_au))
     res = pcg(lambda v: normal_matvec(A, D, delta, v),
               lambda v: precond_inv_apply(F, delta, v),
               xi, eta, maxit, forced_iters)
     dy = res.x
     dx = D * (A.T @ dy - r_d - xi_au)
-    dz = (r_xz - z * dx) / x
-    return Direction(dx=dx, dy=dy, dz=dz, pcg_iters=res.iters, pcg_res=res.res_norm)
+    if kind is None:
+        dz = (r_xz - z * dx) / x
+        return Direction(dx=dx, dy=dy, dz=dz, pcg_iters=res.iters, pcg_res=res.res_norm)
+    dz = np.zeros_like(x)
+    dz[ij] = (r_xz[ij] - z[ij] * dx[ij]) / x[ij]
+    dw = np.zeros_like(x)
+    dw[jj] = r_u[jj] - dx[jj]
+    ds = np.zeros_like(x)
+    ds[jj] = (r_ws[jj] - s[jj] * dw[jj]) / w[jj]
+    return Direction(dx=dx, dy=dy, dz=dz, pcg_iters=res.iters, pcg_res=res.res_norm, dw=dw, ds=ds)
 
 
 def step_length(v: np.ndarray, dv: np.ndarray) -> float:
@@ -292,6 +340,31 @@ def step_length(v: np.ndarray, dv: np.ndarray) -> float:
     if np.any(neg):
         a = min(1.0, float(np.min(-v[neg] / dv[neg])))
     return 0.995 * a
+
+
+def step_lengths(x, dx, z, dz, kind=None, w=None, dw=None, s=None, ds=None):
+    """(alpha_p, alpha_d) of Eq. stepsize-p / stepsize-d.  alpha_p covers x on
+    I and J (free x_F are unbounded) and the slack w on J; alpha_d covers z on
+    I and J and s on J.  For I = {1..n} these are the steps of x and z."""
+    if kind is None:
+        return step_length(x, dx), step_length(z, dz)
+    ij, jj = kind != KIND_F, kind == KIND_J
+    ap = step_length(np.concatenate([x[ij], w[jj]]), np.concatenate([dx[ij], dw[jj]]))
+    ad = step_length(np.concatenate([z[ij], s[jj]]), np.concatenate([dz[ij], ds[jj]]))
+    return ap, ad
+
+
+def duality_measure(x, z, kind=None, w=None, s=None) -> float:
+    """mu = (x_IJ^T z_IJ + w_J^T s_J) / (|IJ| + |J|) (Algorithm 5, fourth step);
+    x^T z / n for I = {1..n}.  With no bounded variable at all (every x_j
+    free) there is no complementarity and mu = 0."""
+    if kind is None:
+        return float(x @ z) / x.shape[0]
+    ij, jj = kind != KIND_F, kind == KIND_J
+    count = int(ij.sum()) + int(jj.sum())
+    if count == 0:
+        return 0.0
+    return (float(x[ij] @ z[ij]) + float(w[jj] @ s[jj])) / count
 
 
 # ---------------------------------------------------------------------------
@@ -345,27 +418,44 @@ class Result:
     rho: float
     delta: float
     trace: list
+    w: np.ndarray | None = None     # slack u - x and its dual (box-constrained
+    s: np.ndarray | None = None     #   variables; zero outside J)
 
 
-def kkt_measures(A, b, c, q, x, y, z):
+def kkt_measures(A, b, c, q, x, y, z, kind=None, u=None, w=None, s=None):
     """READING of the termination test (Algorithm 3 tests absolute norms; the
     experiments speak of relative infeasibilities): relative primal and dual
-    infeasibility and the duality measure mu = x^T z / n."""
-    rel_p = float(np.linalg.norm(A @ x - b)) / (1.0 + float(np.linalg.norm(b)))
-    rel_d = float(np.linalg.norm(c + q * x - A.T @ y - z)) / (1.0 + float(np.linalg.norm(c)))
-    mu = float(x @ z) / x.shape[0]
-    return rel_p, rel_d, mu
+    infeasibility and the duality measure mu = x^T z / n.
+    With free and box-constrained variables the primal residual stacks
+    Ax - b with the slack equation x_J + w_J - u_J (third block row of the
+    system behind Eq. Newton-free-box), relative to 1 + ||(b, u_J)||; the dual
+    residual is c + Qx - A^T y - z + s (dual constraint of (D~)); mu is
+    duality_measure()."""
+    if kind is None:
+        rel_p = float(np.linalg.norm(A @ x - b)) / (1.0 + float(np.linalg.norm(b)))
+        rel_d = float(np.linalg.norm(c + q * x - A.T @ y - z)) / (1.0 + float(np.linalg.norm(c)))
+        mu = float(x @ z) / x.shape[0]
+        return rel_p, rel_d, mu
+    jj = kind == KIND_J
+    rp = np.concatenate([A @ x - b, x[jj] + w[jj] - u[jj]])
+    rel_p = float(np.linalg.norm(rp)) / (1.0 + float(np.linalg.norm(np.concatenate([b, u[jj]]))))
+    rel_d = float(np.linalg.norm(c + q * x - A.T @ y - z + s)) / (1.0 + float(np.linalg.norm(c)))
+    return rel_p, rel_d, duality_measure(x, z, kind, w, s)
 
 
-def duality_gap(b, c, q, x, y):
-    """|pobj - dobj| / (1 + |pobj|) with the objectives of (P) and (D)."""
+def duality_gap(b, c, q, x, y, kind=None, u=None, s=None):
+    """|pobj - dobj| / (1 + |pobj|) with the objectives of (P) and (D), or of
+    (P~) and (D~), whose dual objective also subtracts u^T s."""
     pobj = 0.5 * float(x @ (q * x)) + float(c @ x)
     dobj = float(b @ y) - 0.5 * float(x @ (q * x))
+    if kind is not None:
+        jj = kind == KIND_J
+        dobj -= float(u[jj] @ s[jj])
     return abs(pobj - dobj) / (1.0 + abs(pobj))
 
 
 def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int = 0,
-          record: bool = False) -> Result:
+          record: bool = False, kind=None, u=None, s0=None, w0=None) -> Result:
     """Nys-IP-PMM from a given strictly interior start (Algorithm 6).
 
     READING (start): the workloads supply a strictly feasible interior point
@@ -374,7 +464,8 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     Warm start (resume): lam0, zeta0 replace lambda^0, zeta^0, opt.rho0 and
     opt.delta0 carry the PMM parameters, and k0 is the index of the first IPM
     iteration (it selects Omega_k).  With record=True every trace entry also
-    holds the state (x, y, z, lambda, zeta) at the top of its iteration.
+    holds the state (x, y, z, lambda, zeta) at the top of its iteration
+    (followed by w, s for problems with box-constrained variables).
     READING (PEU, which the paper only cites): after every iteration the
     estimates follow the iterate, lambda <- y and zeta <- x (the proximal
     centres are re-centred), and both regularisation parameters decay with
@@ -382,22 +473,38 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     mu_{k+1}), rho <- max(floor, (1 - r_mu) rho), delta <- max(floor,
     (1 - r_mu) delta).  (Keeping the estimates fixed until the infeasibility
     drops by 5% never re-centres them from a feasible start, where the
-    infeasibility starts at zero, and costs 1.5-2x more IPM iterations.)"""
+    infeasibility starts at zero, and costs 1.5-2x more IPM iterations.)
+
+    Free and box-constrained variables (problems (P~)/(D~)): `kind` holds
+    KIND_I, KIND_F or KIND_J per variable, u the upper bounds (read on J
+    only), s0 the start of the bound multipliers s (read on J only, > 0) and
+    w0 the start of the slack w (default u - x0 on J).  z0 is ignored on F
+    (z_F = 0).  The iteration follows Algorithm 5 with the predictor
+    right-hand sides of Eq. predictor-RHS and the corrector right-hand sides
+    of Eq. corrector-RHS; w moves with the primal step, s with the dual one."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     x, y, z = x0.astype(np.float64).copy(), y0.astype(np.float64).copy(), z0.astype(np.float64).copy()
+    w = s = None
+    box = kind is not None
+    if box:
+        kind = np.asarray(kind, dtype=np.int8)
+        ij, jj = kind != KIND_F, kind == KIND_J
+        u = np.where(jj, np.asarray(u, dtype=np.float64), 0.0)       # u_{I u F} = 0
+        z[~ij] = 0.0                                                 # z_F = 0
+        w = np.where(jj, (u - x) if w0 is None else np.asarray(w0, dtype=np.float64), 0.0)
+        s = np.where(jj, np.asarray(s0, dtype=np.float64), 0.0)
     lam_pmm = y.copy() if lam0 is None else np.asarray(lam0, dtype=np.float64).copy()
     zeta = x.copy() if zeta0 is None else np.asarray(zeta0, dtype=np.float64).copy()
     rho, delta = opt.rho0, opt.delta0
     ell = min(opt.ell, m)
-    mu = float(x @ z) / n
     trace, pcg_counts = [], []
     status = "max_iter"
     forced = list(opt.forced_pcg) if opt.forced_pcg is not None else None
     k = 0
-    rel_p = rel_d = float("nan")
+    rel_p = rel_d = mu = float("nan")
     while True:
-        rel_p, rel_d, mu = kkt_measures(A, b, c, q, x, y, z)
+        rel_p, rel_d, mu = kkt_measures(A, b, c, q, x, y, z, kind, u, w, s)
         if opt.forced_ipm is not None:
             if k >= opt.forced_ipm:
                 status = "converged" if (rel_p <= opt.tol and rel_d <= opt.tol and mu <= opt.tol) else "forced"
@@ -409,33 +516,56 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
             break
         state_lam, state_zeta = lam_pmm.copy(), zeta.copy()
         x_top, y_top, z_top = x.copy(), y.copy(), z.copy()
-        D = scaling_D(x, z, q, rho)
+        w_top, s_top = (w.copy(), s.copy()) if box else (None, None)
+        D = scaling_D(x, z, q, rho, kind, w, s)
         Omega = gaussian_omega(opt.seed, k0 + k, m, ell)
         F = nystrom(A, D, Omega)
         eta = pcg_tolerance(mu)
-        # Predictor (Algorithm 5, first step; Eq. predictor-RHS with I = all).
+        # Predictor (Algorithm 5, first step; Eq. predictor-RHS).
         Ax, Aty = A @ x, A.T @ y
-        r_d = c + q * x - Aty - z + rho * (x - zeta)
         r_p = b - Ax - delta * (y - lam_pmm)
-        r_xz = -x * z
+        if box:
+            r_d = c + q * x - Aty - z + s + rho * (x - zeta)
+            r_u = np.where(jj, u - x - w, 0.0)
+            r_xz = np.where(ij, -x * z, 0.0)
+            r_ws = np.where(jj, -w * s, 0.0)
+        else:
+            r_d = c + q * x - Aty - z + rho * (x - zeta)
+            r_u = r_ws = None
+            r_xz = -x * z
         fp = forced.pop(0) if forced else None
-        pred = newton_direction(A, x, z, D, delta, r_d, r_p, r_xz, F, eta, opt.max_pcg_iter, fp)
-        ap_bar = step_length(x, pred.dx)
-        ad_bar = step_length(z, pred.dz)
-        mu_aff = float((x + ap_bar * pred.dx) @ (z + ad_bar * pred.dz)) / n      # Eq. mu-aff
-        mu_tilde = mu_aff ** 3 / mu ** 2
+        pred = newton_direction(A, x, z, D, delta, r_d, r_p, r_xz, F, eta, opt.max_pcg_iter, fp,
+                                kind, w, s, r_u, r_ws)
+        ap_bar, ad_bar = step_lengths(x, pred.dx, z, pred.dz, kind, w, pred.dw, s, pred.ds)
+        if box:                                                               # Eq. mu-aff
+            mu_aff = duality_measure(x + ap_bar * pred.dx, z + ad_bar * pred.dz, kind,
+                                     w + ap_bar * pred.dw, s + ad_bar * pred.ds)
+        else:
+            mu_aff = float((x + ap_bar * pred.dx) @ (z + ad_bar * pred.dz)) / n
+        mu_tilde = mu_aff ** 3 / mu ** 2 if mu > 0.0 else 0.0
         # Corrector (Eq. corrector-RHS).
         zero_n, zero_m = np.zeros(n), np.zeros(m)
-        r_xz_c = mu_tilde - pred.dx * pred.dz
+        if box:
+            r_xz_c = np.where(ij, mu_tilde - pred.dx * pred.dz, 0.0)
+            r_ws_c = np.where(jj, mu_tilde - pred.dw * pred.ds, 0.0)
+        else:
+            r_xz_c = mu_tilde - pred.dx * pred.dz
+            r_ws_c = None
         fc = forced.pop(0) if forced else None
-        corr = newton_direction(A, x, z, D, delta, zero_n, zero_m, r_xz_c, F, eta, opt.max_pcg_iter, fc)
+        corr = newton_direction(A, x, z, D, delta, zero_n, zero_m, r_xz_c, F, eta, opt.max_pcg_iter, fc,
+                                kind, w, s, zero_n if box else None, r_ws_c)
         dx, dy, dz = pred.dx + corr.dx, pred.dy + corr.dy, pred.dz + corr.dz
-        alpha_p = step_length(x, dx)
-        alpha_d = step_length(z, dz)
+        dw = ds = None
+        if box:
+            dw, ds = pred.dw + corr.dw, pred.ds + corr.ds
+        alpha_p, alpha_d = step_lengths(x, dx, z, dz, kind, w, dw, s, ds)
         x = x + alpha_p * dx
         y = y + alpha_d * dy
         z = z + alpha_d * dz
-        mu_new = float(x @ z) / n
+        if box:
+            w = w + alpha_p * dw
+            s = s + alpha_d * ds
+        mu_new = duality_measure(x, z, kind, w, s)
         pcg_counts += [pred.pcg_iters, corr.pcg_iters]
         rec = IterRecord(k=k0 + k, mu=mu, rel_p=rel_p, rel_d=rel_d, rho=rho, delta=delta, nu=F.nu,
                          lam_max=float(F.lam[0]), lam_min=float(F.lam[-1]),
@@ -443,9 +573,12 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
                          pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters)
         if record:
             rec.state = (x_top, y_top, z_top, state_lam, state_zeta)
+            if box:
+                rec.state += (w_top, s_top)
         trace.append(rec)
         # PEU (READING, see docstring).
-        r_mu = abs(mu_new - mu) / max(mu, mu_new)
+        den = max(mu, mu_new)
+        r_mu = abs(mu_new - mu) / den if den > 0.0 else 0.0
         lam_pmm = y.copy()
         zeta = x.copy()
         delta = max(opt.reg_floor, (1.0 - r_mu) * delta)
@@ -453,12 +586,17 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         mu = mu_new
         k += 1
     return Result(x=x, y=y, z=z, status=status, ipm_iters=k, pcg_iters=pcg_counts,
-                  rel_p=rel_p, rel_d=rel_d, mu=mu, rel_gap=duality_gap(b, c, q, x, y),
-                  rho=rho, delta=delta, trace=trace)
+                  rel_p=rel_p, rel_d=rel_d, mu=mu, rel_gap=duality_gap(b, c, q, x, y, kind, u, s),
+                  rho=rho, delta=delta, trace=trace, w=w, s=s)
 
 
 def solve_qp(qp, opt: Options, **kw) -> Result:
-    """Convenience wrapper over a workload record with fields A, b, c, q, x0, y0, z0."""
+    """Convenience wrapper over a workload record with fields A, b, c, q, x0, y0, z0
+    (and kind, u, s0 when the record has box-constrained or free variables)."""
+    if getattr(qp, "kind", None) is not None:
+        kw.setdefault("kind", qp.kind)
+        kw.setdefault("u", qp.u)
+        kw.setdefault("s0", qp.s0)
     return solve(qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0, opt, **kw)
 
 

@@ -15,6 +15,10 @@ prescribed singular-value spectrum:
 The feasible start is built so that the start point is strictly interior and
 primal/dual feasible: x0 ~ U[0.5, 1.5], b = A x0, y0 ~ N(0, 1),
 z0 ~ U[0, 1] clamped to >= 1e-3, c = A^T y0 + z0 - Q x0.
+
+Problems with free and box-constrained variables, (P~)/(D~), carry a kind per
+variable (KIND_I: x_j >= 0, KIND_F: free, KIND_J: 0 <= x_j <= u_j), the upper
+bounds u and the start s0 of the bound multipliers; see `box_qp`.
 """
 from __future__ import annotations
 
@@ -22,6 +26,7 @@ import dataclasses
 import numpy as np
 
 Z0_FLOOR = 1e-3
+KIND_I, KIND_F, KIND_J = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -36,6 +41,9 @@ class QP:
     y0: np.ndarray
     z0: np.ndarray
     name: str = ""
+    kind: np.ndarray | None = None    # int8 per variable (None: every x_j >= 0)
+    u: np.ndarray | None = None       # upper bounds (0 outside KIND_J)
+    s0: np.ndarray | None = None      # start of the bound multipliers (0 outside KIND_J)
 
     @property
     def m(self) -> int:
@@ -73,6 +81,46 @@ def feasible_qp(rng: np.random.Generator, A: np.ndarray, q: np.ndarray, name: st
     b = A @ x0
     c = A.T @ y0 + z0 - q * x0
     return QP(A=A, b=b, c=c, q=q, x0=x0, y0=y0, z0=z0, name=name)
+
+
+def feasible_box_qp(rng: np.random.Generator, A: np.ndarray, q: np.ndarray, frac_free: float,
+                    frac_box: float, name: str = "") -> QP:
+    """Feasible interior start for (P~)/(D~): a random floor(frac_free n)
+    variables are free, floor(frac_box n) box-constrained, the rest
+    non-negative.  x0 ~ U[0.5, 1.5] on I and J, N(0, 1) on F;
+    u_J = x0_J + U[0.5, 1.5] (so the slack u - x0 lies in [0.5, 1.5]);
+    z0 ~ U[0, 1] clamped to >= 1e-3 on I and J, 0 on F; s0 likewise on J,
+    0 elsewhere; y0 ~ N(0, 1); b = A x0 and c = A^T y0 + z0 - s0 - Q x0, so
+    the start satisfies both equality constraints."""
+    m, n = A.shape
+    perm = rng.permutation(n)
+    nf, nb = int(frac_free * n), int(frac_box * n)
+    kind = np.full(n, KIND_I, dtype=np.int8)
+    kind[perm[:nf]] = KIND_F
+    kind[perm[nf:nf + nb]] = KIND_J
+    free, box = kind == KIND_F, kind == KIND_J
+    x0 = np.where(free, rng.standard_normal(n), rng.uniform(0.5, 1.5, n))
+    u = np.where(box, x0 + rng.uniform(0.5, 1.5, n), 0.0)
+    y0 = rng.standard_normal(m)
+    z0 = np.where(free, 0.0, np.maximum(rng.uniform(0.0, 1.0, n), Z0_FLOOR))
+    s0 = np.where(box, np.maximum(rng.uniform(0.0, 1.0, n), Z0_FLOOR), 0.0)
+    b = A @ x0
+    c = A.T @ y0 + z0 - s0 - q * x0
+    return QP(A=A, b=b, c=c, q=q, x0=x0, y0=y0, z0=z0, name=name, kind=kind, u=u, s0=s0)
+
+
+def box_qp(seed: int, m: int, n: int, frac_free: float = 0.1, frac_box: float = 0.3,
+           sigma_kind: str = "inv", q_kind: str = "uniform") -> QP:
+    """Dense QP with free and box-constrained variables (problems (P~)/(D~)):
+    the spectral constraint matrix of `spectral_qp` with the start of
+    `feasible_box_qp`."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(1, m + 1, dtype=np.float64)
+    sigma = {"inv": 1.0 / i, "pow0.8": i ** -0.8, "exp200": np.exp(-i / 200.0) + 1e-3}[sigma_kind]
+    A = spectrum_matrix(rng, m, n, sigma)
+    q = make_q(rng, n, q_kind)
+    return feasible_box_qp(rng, A, q, frac_free, frac_box,
+                           name=f"box-{sigma_kind}-{m}x{n}-f{frac_free}-b{frac_box}-s{seed}")
 
 
 def spectral_qp(seed: int, m: int, n: int, sigma_kind: str, q_kind: str = "uniform") -> QP:
@@ -137,6 +185,12 @@ def low_rank_qp(seed: int, m: int, n: int, rank: int, q_kind: str = "uniform") -
 def workload_small(seed: int = 1235) -> QP:
     """m=200, n=500, sigma_i = 1/i, q ~ U[0,1]; solved with ell=20, tol 1e-6."""
     return spectral_qp(seed, 200, 500, "inv", "uniform")
+
+
+def workload_box(seed: int = 1240, m: int = 200, n: int = 500) -> QP:
+    """The m=200, n=500 shape (sigma_i = 1/i, q ~ U[0,1]) with 10% free and
+    30% box-constrained variables; solved with ell=20, tol 1e-6."""
+    return box_qp(seed, m, n, 0.1, 0.3, "inv", "uniform")
 
 
 def workload_fp64(seed: int = 1236) -> QP:
