@@ -40,6 +40,9 @@ import numpy as np  # noqa: E402
 WORKLOADS = {
     "small-fp64": dict(form="fp64", m=200, n=500, ell=20, tol=1e-6, gen="small",
                        desc="m=200, n=500, sigma_i=1/i, q~U[0,1], ell=20, tol 1e-6, FP64 form"),
+    "box-200x500": dict(form="box", m=200, n=500, ell=20, tol=1e-6, gen="box",
+                        desc="m=200, n=500, sigma_i=1/i, q~U[0,1], 10% free and 30% box-constrained variables "
+                             "(problem (P~)), ell=20, tol 1e-6, FP64 form"),
     "fp64-5000x20000": dict(form="fp64", m=5000, n=20000, ell=100, tol=1e-8, gen="fp64",
                             desc="m=5000, n=20000, sigma_i=i^-0.8, q 50% zero, ell=100, tol 1e-8, FP64 form"),
     "precision-20000x100000": dict(form="bf16", m=20000, n=100000, ell=400, tol=1e-6, gen="device-exp200",
@@ -151,6 +154,8 @@ def host_workload(w, rank):
     off = 1000 * rank
     if g == "small":
         return [synth.workload_small(1235 + off)]
+    if g == "box":
+        return [synth.workload_box(1240 + off)]
     if g == "fp64":
         return [synth.workload_fp64(1236 + off)]
     if g == "batch":
@@ -183,11 +188,12 @@ def device_workload(w, rank, dev, host_gen=False):
 
 # ------------------------------------------------------------------ CPU oracle legs
 
-def oracle_component_times(A64, b, c, q, x0, y0, z0, ell, tol, seed):
+def oracle_component_times(A64, b, c, q, x0, y0, z0, ell, tol, seed, box=None):
     from oracle import nys_oracle as O
     m, n = A64.shape
     t0 = time.perf_counter()
-    O.solve(A64, b, c, q, x0, y0, z0, O.Options(tol=tol, ell=ell, seed=seed, forced_ipm=1, forced_pcg=[0, 0]))
+    O.solve(A64, b, c, q, x0, y0, z0, O.Options(tol=tol, ell=ell, seed=seed, forced_ipm=1, forced_pcg=[0, 0]),
+            **(box or {}))
     t_ipm = time.perf_counter() - t0
     D = O.scaling_D(x0, z0, q, 1.0)
     F = O.nystrom(A64, D, O.gaussian_omega(seed, 0, m, min(ell, m)))
@@ -208,7 +214,7 @@ def cpu_baseline(problems, w, runs, seed):
     qp = problems[0]
     A64 = qp["A64"]
     t_ipm, t_pcg = oracle_component_times(A64, qp["b"], qp["c"], qp["q"], qp["x0"], qp["y0"], qp["z0"],
-                                          qp["ell"], w["tol"], seed)
+                                          qp["ell"], w["tol"], seed, qp.get("box"))
     ipm, pcg = runs[0]["ipm_iters"], runs[0]["pcg_iters_total"]
     est = ipm * t_ipm + pcg * t_pcg
     per_step = len(problems)
@@ -216,7 +222,7 @@ def cpu_baseline(problems, w, runs, seed):
         t0 = time.perf_counter()
         for p in problems:
             O.solve(p["A64"], p["b"], p["c"], p["q"], p["x0"], p["y0"], p["z0"],
-                    O.Options(tol=w["tol"], ell=p["ell"], seed=seed))
+                    O.Options(tol=w["tol"], ell=p["ell"], seed=seed), **(p.get("box") or {}))
         full = time.perf_counter() - t0
         return {"value": per_step / full / per_step, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
                 "sample": f"whole oracle solve(s) of the same workload ({per_step} QP, {full:.2f} s)"}
@@ -322,7 +328,10 @@ def main():
         dev_probs = []
         for qp in host_probs:
             ell = min(w["ell"], max(1, qp.m // 4)) if form == "batch" else w["ell"]
-            dev_probs.append(tuple(T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0)) + (ell,))
+            pr = tuple(T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0)) + (ell,)
+            if qp.kind is not None:      # problem (P~): kinds, upper bounds, start of s
+                pr = pr + (dict(kind=T(qp.kind), u=T(qp.u), s0=T(qp.s0)),)
+            dev_probs.append(pr)
     else:
         dev_probs = [device_workload(w, rank, dev, args.host_gen) + (w["ell"],)]
     mmax = max(p[0].shape[0] for p in dev_probs)
@@ -341,7 +350,7 @@ def main():
                 return [r[3] for r in nys.nys_solve_batched(h, dev_probs)]
             out = []
             for pr in dev_probs:
-                x, y, z, info = nys.nys_solve(h, *pr[:7])
+                x, y, z, info = nys.nys_solve(h, *pr[:7], **(pr[8] if len(pr) > 8 else {}))
                 if form == "diff":
                     g = 2.0 * (x - T(host_probs[len(out)].target))
                     nys.nys_adjoint(h, pr[0], pr[3], x, y, z, info, g, eta=1e-10)
@@ -426,22 +435,25 @@ def main():
             roofline = fp64_operator_roofline(nys, h, A0, stream)
         # ---- e2e: the same solves through the C ABI from pinned host buffers
         e2e = None
-        if form in ("fp64", "bf16", "fp8"):
+        if form in ("fp64", "box", "bf16", "fp8"):
             pin = lambda t: t.detach().cpu().pin_memory()
             hp = [tuple(pin(t) for t in pr[:7]) for pr in dev_probs]
-            nys.nys_solve(h, *hp[0])
+            hbox = [{k: pin(t) for k, t in pr[8].items()} if len(pr) > 8 else {} for pr in dev_probs]
+            nys.nys_solve(h, *hp[0], **hbox[0])
             barrier()
             t0 = time.perf_counter()
             for _ in range(args.steps):
-                for pr in hp:
-                    nys.nys_solve(h, *pr)
+                for pr, bx in zip(hp, hbox):
+                    nys.nys_solve(h, *pr, **bx)
             e2e_s = time.perf_counter() - t0
             if world > 1:
                 te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
                 dist.all_reduce(te, op=dist.ReduceOp.MAX)
                 e2e_s = float(te[0])
-            h2d = sum(sum(t.numel() * t.element_size() for t in pr) for pr in hp)
-            d2h = sum(8 * (2 * pr[0].shape[1] + pr[0].shape[0]) for pr in hp)
+            h2d = sum(sum(t.numel() * t.element_size() for t in pr) for pr in hp) + \
+                sum(sum(t.numel() * t.element_size() for t in bx.values()) for bx in hbox)
+            d2h = sum(8 * (2 * pr[0].shape[1] + pr[0].shape[0]) for pr in hp) + \
+                sum(8 * 2 * pr[0].shape[1] for pr, bx in zip(hp, hbox) if bx)
             e2e = {"value": args.steps * per_step * world / e2e_s, "unit": "QP solves/s",
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         else:
@@ -471,7 +483,9 @@ def main():
             probs = []
             if host_probs is not None:
                 for qp, pr in zip(host_probs[:4], dev_probs[:4]):
-                    probs.append(dict(A64=qp.A, b=qp.b, c=qp.c, q=qp.q, x0=qp.x0, y0=qp.y0, z0=qp.z0, ell=pr[7]))
+                    box = dict(kind=qp.kind, u=qp.u, s0=qp.s0) if qp.kind is not None else None
+                    probs.append(dict(A64=qp.A, b=qp.b, c=qp.c, q=qp.q, x0=qp.x0, y0=qp.y0, z0=qp.z0, ell=pr[7],
+                                      box=box))
             else:
                 pr = dev_probs[0]
                 probs.append(dict(A64=pr[0].double().cpu().numpy(), b=pr[1].cpu().numpy(), c=pr[2].cpu().numpy(),
@@ -482,7 +496,8 @@ def main():
             "metric": "QP solves/s to KKT tol", "value": value, "unit": "QP solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "bf16": "bf16", "fp8": "fp8e4m3", "batch": "f64", "diff": "f64"}[form],
+            "dtype": {"fp64": "f64", "box": "f64", "bf16": "bf16", "fp8": "fp8e4m3", "batch": "f64",
+                      "diff": "f64"}[form],
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",

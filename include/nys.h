@@ -3,6 +3,9 @@
  *
  * The library solves separable convex QPs (Section 1, problems (P)/(D)):
  *     min 1/2 x^T Q x + c^T x   s.t.  A x = b,  x >= 0,     Q = diag(q), q >= 0,
+ * and their generalisation (P~)/(D~) with free variables (x_F free) and
+ * box-constrained variables (0 <= x_J <= u_J) of the section on free and
+ * box-constrained variables (nys_problem.var_kind),
  * by the randomized-Nystrom-preconditioned IP-PMM of arxiv 2404.14524
  * (Algorithm 6 with the predictor-corrector of Algorithm 5 and the Newton
  * solve of Algorithm 4).  Every step of the solve runs in this library's CUDA
@@ -87,6 +90,22 @@ typedef struct {
     int k0;
     int ell;                      /* sketch size for this problem (0 = the handle's), */
                                   /* clamped to the handle's ell and to m             */
+    /* Free and box-constrained variables, problems (P~)/(D~).  var_kind NULL:
+     * every x_j >= 0 (problem (P)); u, w0, s0 are then ignored.  Otherwise n
+     * kinds: 0 = x_j >= 0 (set I), 1 = free (F), 2 = 0 <= x_j <= u_j (J).
+     * The iteration is Algorithm 5 with Algorithm 4 in its general form: the
+     * slack w = u - x and the multiplier s of x_J <= u_J move with the primal
+     * and the dual step; z0 is ignored on F (z_F = 0).  On J, u must be
+     * finite and s0, w0 positive (u and s0 are required when some kind is 2;
+     * entries outside J are ignored).  An invalid kind or J entry gives
+     * NYS_ERR_ARG (checked on the device before the first iteration).
+     * Termination: ||(Ax - b, x_J + w_J - u_J)|| / (1 + ||(b, u_J)||),
+     * ||c + Qx - A^T y - z + s|| / (1 + ||c||) and
+     * mu = (x_IJ^T z_IJ + w_J^T s_J) / (|I u J| + |J|) all <= tol. */
+    const signed char* var_kind;  /* n, or NULL                                       */
+    const double* u;              /* n: upper bounds (read on J)                      */
+    const double* w0;             /* n: start of w on J (NULL = u - x0)               */
+    const double* s0;             /* n: start of s on J                               */
 } nys_problem;
 
 /* Result.  x, y, z are caller-allocated outputs (n, m, n) in the same memory
@@ -101,7 +120,7 @@ typedef struct {
     int ipm_iters;
     int pcg_iters_total;
     int refine_steps;
-    double rel_primal;            /* ||Ax - b|| / (1 + ||b||)                          */
+    double rel_primal;            /* ||Ax - b|| / (1 + ||b||)  ((P~): see var_kind)    */
     double rel_dual;              /* ||c + Qx - A^T y - z|| / (1 + ||c||)              */
     double mu;                    /* x^T z / n                                         */
     double rel_gap;               /* |pobj - dobj| / (1 + |pobj|)                      */
@@ -114,6 +133,8 @@ typedef struct {
     int* pcg_log;                 /* optional host array: PCG iterations per Newton   */
     int pcg_log_cap;              /*   solve, in order (capacity in entries)           */
     int pcg_log_len;              /* entries written                                   */
+    double *w, *s;                /* n each, NULL = not wanted: final slack and bound */
+                                  /*   multiplier of a (P~) problem (0 outside J)     */
 } nys_result;
 
 /* Fill *opt with the defaults listed above. */
@@ -155,7 +176,8 @@ int nys_destroy(nys_handle h);
  * problems, FP64 A; x, y, z, rho, delta are read from r[i]).  Device arrays,
  * QPs concatenated in order: dL_dx, dL_dc, dL_dq (sum n_i), dL_db (sum m_i),
  * dL_dA (sum m_i n_i, each QP row-major m_i x n_i; FP64).  Any output may be
- * NULL.  Returns the worst status over the QPs. */
+ * NULL.  Problems (P) only: a problem with var_kind set gives NYS_ERR_ARG.
+ * Returns the worst status over the QPs. */
 int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result* r, const double* dL_dx,
                 double eta, double* dL_dc, double* dL_db, double* dL_dq, double* dL_dA);
 

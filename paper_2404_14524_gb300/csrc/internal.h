@@ -246,6 +246,9 @@ cudaError_t ipm_residuals_f64(cudaStream_t st, int m, int n, const double* b, co
                               const double* lam, const double* zeta, double rho, double delta,
                               double* r_d, double* r_p, double* r_xz, double* red_out,
                               RedBuf red);
+// m-part alone: r_p = b - Ax - delta (y - lam); red_out[0] = ||b - Ax||^2 (device)
+cudaError_t ipm_residuals_m_f64(cudaStream_t st, int m, const double* b, const double* Ax, const double* y,
+                                const double* lam, double delta, double* r_p, double* red_out, RedBuf red);
 // t = D (r_d - r_xz / x)   (null r_d means zero)
 cudaError_t newton_rhs_f64(cudaStream_t st, int n, const double* D, const double* r_d,
                            const double* r_xz, const double* x, double* t);
@@ -269,6 +272,50 @@ cudaError_t add_dirs_f64(cudaStream_t st, int m, int n, const double* dxp, const
 // x += ap dx; z += ad dz (n);  y += ad dy (m)
 cudaError_t ipm_update_f64(cudaStream_t st, int m, int n, double ap, double ad, const double* dx,
                            const double* dy, const double* dz, double* x, double* y, double* z);
+// ---------------------------------------------------------------- free and box-constrained variables
+// Problems (P~)/(D~): kind per variable vk[j] in {0 = I (x_j >= 0), 1 = F
+// (free), 2 = J (0 <= x_j <= u_j)}, slack w = u - x and multiplier s on J.
+// Every kernel keeps z = 0 on F and u = w = s = 0 outside J.
+struct BoxVectors {
+  const signed char* vk = nullptr;
+  const double* w = nullptr;
+  const double* s = nullptr;
+};
+// In place on the handle's copies: z_F = 0; on J w = w0 (has_w0) or u - x,
+// s = s0; elsewhere u = w = s = 0.  out[0] = |I u J| + |J|, out[1] = ||u_J||^2,
+// out[2] = count of invalid entries (device).
+cudaError_t box_start_f64(cudaStream_t st, int n, const signed char* vk, double* u, const double* x, double* z,
+                          double* w, double* s, int has_u, int has_w0, int has_s0, double* out, RedBuf red);
+// D = 1 / (q + Theta^{-1} + rho), Theta^{-1} = z/x on I, z/x + s/w on J, 0 on F
+cudaError_t box_scaling_f64(cudaStream_t st, int n, const signed char* vk, const double* x, const double* z,
+                            const double* w, const double* s, const double* q, double rho, double* D);
+// n-part of Eq. predictor-RHS: r_d, r_u, r_xz, r_ws; out[0] = ||c + Qx - A^T y - z + s||^2,
+// out[1] = x_IJ^T z_IJ + w_J^T s_J, out[2] = ||u_J - x_J - w_J||^2 (device)
+cudaError_t box_residuals_n_f64(cudaStream_t st, int n, const signed char* vk, const double* c, const double* q,
+                                const double* u, const double* x, const double* z, const double* w,
+                                const double* s, const double* Aty, const double* zeta, double rho, double* r_d,
+                                double* r_u, double* r_xz, double* r_ws, double* out, RedBuf red);
+// t = D (r_d + xi_au) of Algorithm 4 (null r_d / r_u mean zero)
+cudaError_t box_newton_rhs_f64(cudaStream_t st, int n, const BoxVectors& bx, const double* D, const double* r_d,
+                               const double* r_u, const double* r_xz, const double* r_ws, const double* x,
+                               double* t);
+// dx = D (g - r_d - xi_au), dw, dz, ds of Algorithm 4 (g = A^T dy)
+cudaError_t box_newton_back_f64(cudaStream_t st, int n, const BoxVectors& bx, const double* D, const double* g,
+                                const double* r_d, const double* r_u, const double* r_xz, const double* r_ws,
+                                const double* x, const double* z, double* dx, double* dz, double* dw,
+                                double* ds);
+// out[0] = min ratio over (x, dx) on I u J and (w, dw) on J; out[1] over (z, dz), (s, ds)
+cudaError_t box_step_ratios_f64(cudaStream_t st, int n, const signed char* vk, const double* x, const double* dx,
+                                const double* w, const double* dw, const double* z, const double* dz,
+                                const double* s, const double* ds, double* out, RedBuf red);
+// out = (x + ap dx)_IJ^T (z + ad dz)_IJ + (w + ap dw)_J^T (s + ad ds)_J
+cudaError_t box_mu_aff_f64(cudaStream_t st, int n, const signed char* vk, const double* x, const double* dx,
+                           const double* z, const double* dz, const double* w, const double* dw, const double* s,
+                           const double* ds, double ap, double ad, double* out, RedBuf red);
+// r_xz = mu_t - dxp dzp on I u J, r_ws = mu_t - dwp dsp on J (0 elsewhere)
+cudaError_t box_corrector_rhs_f64(cudaStream_t st, int n, const signed char* vk, double mu_t, const double* dxp,
+                                  const double* dzp, const double* dwp, const double* dsp, double* r_xz,
+                                  double* r_ws);
 // out = a .* b
 cudaError_t vmul_f64(cudaStream_t st, int len, const double* a, const double* b, double* out);
 // out[i, j] = alpha u_i v_j + beta w_i s_j, row-major m x n (FP32 or FP64 out)

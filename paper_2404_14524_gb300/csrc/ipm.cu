@@ -260,6 +260,14 @@ cudaError_t ipm_residuals_f64(cudaStream_t st, int m, int n, const double* b, co
   return cudaGetLastError();
 }
 
+cudaError_t ipm_residuals_m_f64(cudaStream_t st, int m, const double* b, const double* Ax, const double* y,
+                                const double* lam, double delta, double* r_p, double* red_out, RedBuf red) {
+  count_launches(1);
+  k_res_m<<<grid_for(m), kNT, 0, st>>>(m, b, Ax, y, lam, delta, r_p, red_out, red.part + 4 * 2 * 152,
+                                       red.cnt + 5);
+  return cudaGetLastError();
+}
+
 cudaError_t newton_rhs_f64(cudaStream_t st, int n, const double* D, const double* r_d,
                            const double* r_xz, const double* x, double* t) {
   count_launches(1);

@@ -55,6 +55,12 @@ struct nys_solver {
   double *t_n = nullptr, *g_n = nullptr, *xi = nullptr;
   double *dxp = nullptr, *dyp = nullptr, *dzp = nullptr, *dxc = nullptr, *dyc = nullptr, *dzc = nullptr;
   double* red_out = nullptr;
+  // free and box-constrained variables (problems (P~)/(D~)): kinds, upper
+  // bounds (zero outside J), slack w = u - x, its multiplier s, their
+  // right-hand sides and directions
+  signed char* vk = nullptr;
+  double *uv = nullptr, *w = nullptr, *s = nullptr, *r_u = nullptr, *r_ws = nullptr;
+  double *dwp = nullptr, *dsp = nullptr, *dwc = nullptr, *dsc = nullptr;
   // pinned host mirrors
   double* h_red = nullptr;
   int* h_si = nullptr;
@@ -212,6 +218,16 @@ size_t carve(nys_solver* h, char* base) {
   h->dyc = c.take<double>(M);
   h->dzc = c.take<double>(N);
   h->red_out = c.take<double>(16);
+  h->vk = c.take<signed char>(N);
+  h->uv = c.take<double>(N);
+  h->w = c.take<double>(N);
+  h->s = c.take<double>(N);
+  h->r_u = c.take<double>(N);
+  h->r_ws = c.take<double>(N);
+  h->dwp = c.take<double>(N);
+  h->dsp = c.take<double>(N);
+  h->dwc = c.take<double>(N);
+  h->dsc = c.take<double>(N);
   return c.off;
 }
 
@@ -475,21 +491,53 @@ int run_pcg(nys_solver* h, int m, int n, const double* A, long long lda, const d
   return run_pcg(h, m, n, op, delta, ell, U, ld, lamh, xi, out, eta, max_iter, forced, iters);
 }
 
-// Algorithm 4, first half: xi = r_p + A D (r_d - X^{-1} r_xz) into h->xi.
+// The (P~) terms of one Newton system of Algorithm 4 (free and
+// box-constrained variables): kinds, w, s, the right-hand sides r_u (null:
+// zero, the corrector) and r_ws, and where dw, ds go.  A null BoxTerms
+// pointer means problem (P), every x_j >= 0.
+struct BoxTerms {
+  BoxVectors v;
+  const double* r_u = nullptr;
+  const double* r_ws = nullptr;
+  double* dw = nullptr;
+  double* ds = nullptr;
+};
+
+// t = D (r_d + xi_au) into h->t_n (Algorithm 4, first step)
+int newton_rhs(nys_solver* h, int n, const double* x, const double* D, const double* r_d, const double* r_xz,
+               const BoxTerms* bt) {
+  if (bt) CK(box_newton_rhs_f64(h->st, n, bt->v, D, r_d, bt->r_u, r_xz, bt->r_ws, x, h->t_n));
+  else CK(newton_rhs_f64(h->st, n, D, r_d, r_xz, x, h->t_n));
+  return NYS_OK;
+}
+
+// dx, dz (and dw, ds) from g = A^T dy in h->g_n (Algorithm 4, third step)
+int newton_back(nys_solver* h, int n, const double* x, const double* z, const double* D, const double* r_d,
+                const double* r_xz, const BoxTerms* bt, double* dx, double* dz) {
+  if (bt) CK(box_newton_back_f64(h->st, n, bt->v, D, h->g_n, r_d, bt->r_u, r_xz, bt->r_ws, x, z, dx, dz, bt->dw,
+                                 bt->ds));
+  else CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
+  return NYS_OK;
+}
+
+// Algorithm 4, first half: xi = r_p + A D (r_d + xi_au) into h->xi
+// (xi_au = -X^{-1} r_xz for problem (P)).
 int newton_begin(nys_solver* h, int m, int n, const double* A, long long lda, const double* x,
-                 const double* D, const double* r_d, const double* r_p, const double* r_xz) {
-  CK(newton_rhs_f64(h->st, n, D, r_d, r_xz, x, h->t_n));
+                 const double* D, const double* r_d, const double* r_p, const double* r_xz,
+                 const BoxTerms* bt = nullptr) {
+  const int rc = newton_rhs(h, n, x, D, r_d, r_xz, bt);
+  if (rc != NYS_OK) return rc;
   CK(gemv_n_f64(h->st, m, n, A, lda, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi));
   return NYS_OK;
 }
 
-// Algorithm 4, second half: dx = D (A^T dy - r_d + X^{-1} r_xz), dz = X^{-1} (r_xz - Z dx).
+// Algorithm 4, second half: dx = D (A^T dy - r_d - xi_au), dz = X^{-1} (r_xz - Z dx)
+// (and dw, ds for problem (P~)).
 int newton_end(nys_solver* h, int m, int n, const double* A, long long lda, const double* x,
                const double* z, const double* D, const double* r_d, const double* r_xz, const double* dy,
-               double* dx, double* dz) {
+               double* dx, double* dz, const BoxTerms* bt = nullptr) {
   CK(gemv_t_f64(h->st, m, n, A, lda, dy, nullptr, h->g_n, h->split_buf, h->split_cap));
-  CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
-  return NYS_OK;
+  return newton_back(h, n, x, z, D, r_d, r_xz, bt, dx, dz);
 }
 
 // Algorithm 4: Newton direction through the normal equations.
@@ -602,10 +650,11 @@ LpOperator make_lp_op(nys_solver* h, const Prob& P, int kind, const double* D) {
 
 int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, const double* D, double delta,
               const double* r_d, const double* r_p, const double* r_xz, int ell, double eta, int max_iter,
-              double* dx, double* dy, double* dz, int* iters, int* refine) {
+              double* dx, double* dy, double* dz, int* iters, int* refine, const BoxTerms* bt) {
   const int m = P.m, n = P.n;
-  CK(newton_rhs_f64(h->st, n, D, r_d, r_xz, x, h->t_n));
-  int rc = op_Ax(h, P, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi);
+  int rc = newton_rhs(h, n, x, D, r_d, r_xz, bt);
+  if (rc != NYS_OK) return rc;
+  rc = op_Ax(h, P, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi);
   if (rc != NYS_OK) return rc;
   CK(dot_f64(h->st, m, h->xi, h->xi, h->red_out + 12, h->red));
   rc = sync_scalars_at(h, 12, 1);
@@ -658,7 +707,8 @@ int newton_lp(nys_solver* h, const Prob& P, const double* x, const double* z, co
   CK(cudaMemcpyAsync(dy, h->dyacc, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
   rc = op_Aty(h, P, dy, nullptr, h->g_n);
   if (rc != NYS_OK) return rc;
-  CK(newton_back_f64(h->st, n, D, h->g_n, r_d, r_xz, x, z, dx, dz));
+  rc = newton_back(h, n, x, z, D, r_d, r_xz, bt, dx, dz);
+  if (rc != NYS_OK) return rc;
   *iters = total;
   *refine = steps;
   return warn;
@@ -693,6 +743,10 @@ struct IpmRun {
   const double *b = nullptr, *c = nullptr, *q = nullptr;
   double bnorm = 0.0, cnorm = 0.0, rho = 0.0, delta = 0.0, mu = 0.0, mu_prev = 0.0;
   double rel_p = 0.0, rel_d = 0.0, eta = 0.0, t_pre = 0.0;
+  // problem (P~): free and box-constrained variables present
+  bool box = false;
+  double n_mu = 0.0;            // |I u J| + |J|, the divisor of mu
+  double pnorm = 0.0;           // ||(b, u_J)||, the scale of the primal residual
   int forced_idx = 0, warn = NYS_OK, k = 0, status = NYS_WARN_MAXITER;
   int pcg_before = 0, ref_before = 0;
   bool done = false;
@@ -727,6 +781,20 @@ struct IpmRun {
     log_pcg(req.iters);
     return true;
   }
+  // the (P~) terms of the predictor's and the corrector's Newton systems
+  BoxTerms terms(bool corrector) const {
+    BoxTerms t;
+    t.v.vk = h->vk;
+    t.v.w = h->w;
+    t.v.s = h->s;
+    t.r_u = corrector ? nullptr : h->r_u;
+    t.r_ws = h->r_ws;
+    t.dw = corrector ? h->dwc : h->dwp;
+    t.ds = corrector ? h->dsc : h->dsp;
+    return t;
+  }
+  // residuals of Eq. predictor-RHS at the current iterate and PMM parameters
+  int residuals();
   int start(nys_solver* h_, const nys_problem* p_, nys_result* r_);
   int top();
   int mid();
@@ -806,16 +874,54 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   if (p->zeta0) CK(cudaMemcpyAsync(h->zeta, p->zeta0, sizeof(double) * n, kin, h->st));
   else CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
+  box = p->var_kind != nullptr;
+  if (box) {
+    // kinds, u, w0, s0 into the handle's copies; the start kernel masks them
+    // (u = w = s = 0 outside J, z_F = 0) and counts invalid entries
+    CK(cudaMemcpyAsync(h->vk, p->var_kind, (size_t)n, kin, h->st));
+    if (p->u) CK(cudaMemcpyAsync(h->uv, p->u, sizeof(double) * n, kin, h->st));
+    else CK(cudaMemsetAsync(h->uv, 0, sizeof(double) * n, h->st));
+    if (p->w0) CK(cudaMemcpyAsync(h->w, p->w0, sizeof(double) * n, kin, h->st));
+    if (p->s0) CK(cudaMemcpyAsync(h->s, p->s0, sizeof(double) * n, kin, h->st));
+    else CK(cudaMemsetAsync(h->s, 0, sizeof(double) * n, h->st));
+    CK(box_start_f64(h->st, n, h->vk, h->uv, h->x, h->z, h->w, h->s, p->u != nullptr, p->w0 != nullptr,
+                     p->s0 != nullptr, h->red_out + 10, h->red));
+  }
   CK(dot_f64(h->st, m, b, b, h->red_out + 8, h->red));
   CK(dot_f64(h->st, n, c, c, h->red_out + 9, h->red));
-  int rc = sync_scalars(h, 10);
+  int rc = sync_scalars(h, box ? 13 : 10);
   if (rc != NYS_OK) return r->status = status = rc;
   bnorm = std::sqrt(h->h_red[8]);
   cnorm = std::sqrt(h->h_red[9]);
+  pnorm = bnorm;
+  if (box) {
+    if (h->h_red[12] != 0.0)
+      return r->status = status = fail(h, NYS_ERR_ARG,
+                                       "nys_solve: %.0f invalid entries in var_kind / u / w0 / s0 (kind outside "
+                                       "{0,1,2}; on J: u missing or non-finite, w0 or s0 missing or <= 0)",
+                                       h->h_red[12]);
+    n_mu = h->h_red[10];
+    pnorm = std::sqrt(h->h_red[8] + h->h_red[11]);
+  }
   rho = o.rho0;
   delta = o.delta0;
   status = NYS_WARN_MAXITER;
   done = false;
+  return NYS_OK;
+}
+
+// Eq. predictor-RHS at the current iterate: r_d, r_p, r_xz (and r_u, r_ws).
+// Problem (P): red_out = (||rd||^2, x^T z, ||b - Ax||^2); problem (P~):
+// red_out = (||rd||^2, x_IJ^T z_IJ + w_J^T s_J, ||u_J - x_J - w_J||^2, ||b - Ax||^2).
+int IpmRun::residuals() {
+  if (!box) {
+    CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
+                         rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
+    return NYS_OK;
+  }
+  CK(box_residuals_n_f64(h->st, n, h->vk, c, q, h->uv, h->x, h->z, h->w, h->s, h->Aty, h->zeta, rho, h->r_d,
+                         h->r_u, h->r_xz, h->r_ws, h->red_out, h->red));
+  CK(ipm_residuals_m_f64(h->st, m, b, h->Ax, h->y, h->lam, delta, h->r_p, h->red_out + 3, h->red));
   return NYS_OK;
 }
 
@@ -826,18 +932,19 @@ int IpmRun::top() {
   const nys_options& o = h->opt;
   int rc = op_Ax(h, P, h->x, 0.0, nullptr, h->Ax);
   if (rc == NYS_OK) rc = op_Aty(h, P, h->y, nullptr, h->Aty);
+  if (rc == NYS_OK) rc = residuals();
   if (rc != NYS_OK) { stop(rc); return rc; }
-  CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
-                       rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
-  rc = sync_scalars(h, 3);
+  rc = sync_scalars(h, box ? 4 : 3);
   if (rc != NYS_OK) { stop(rc); return rc; }
-  const double nrd = std::sqrt(h->h_red[0]), nrp = std::sqrt(h->h_red[2]);
-  mu = h->h_red[1] / n;
+  const double nrd = std::sqrt(h->h_red[0]);
+  // (P~): the primal residual stacks Ax - b (red_out[3]) with u_J - x_J - w_J (red_out[2])
+  const double nrp = box ? std::sqrt(h->h_red[3] + h->h_red[2]) : std::sqrt(h->h_red[2]);
+  mu = box ? (n_mu > 0.0 ? h->h_red[1] / n_mu : 0.0) : h->h_red[1] / n;
   if (!std::isfinite(nrd) || !std::isfinite(nrp) || !std::isfinite(mu)) {
     stop(fail(h, NYS_ERR_NUMERIC, "non-finite residual at IPM iteration %d", k));
     return status;
   }
-  rel_p = nrp / (1.0 + bnorm);
+  rel_p = nrp / (1.0 + pnorm);
   rel_d = nrd / (1.0 + cnorm);
   if (k > 0) {
     // PMM parameter update (reading of PEU): re-centre the proximal
@@ -849,8 +956,8 @@ int IpmRun::top() {
     delta = std::max(o.reg_floor, (1.0 - r_mu) * delta);
     rho = std::max(o.reg_floor, (1.0 - r_mu) * rho);
     // predictor right-hand sides with the updated PMM parameters
-    CK(ipm_residuals_f64(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta,
-                         rho, delta, h->r_d, h->r_p, h->r_xz, h->red_out, h->red));
+    rc = residuals();
+    if (rc != NYS_OK) { stop(rc); return rc; }
   }
   // Termination (reading of TC: relative infeasibilities and mu).
   if (o.forced_ipm_iters >= 0) {
@@ -866,7 +973,8 @@ int IpmRun::top() {
 
   // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).
   tk0 = std::chrono::steady_clock::now();
-  CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
+  if (box) CK(box_scaling_f64(h->st, n, h->vk, h->x, h->z, h->w, h->s, q, rho, h->D));
+  else CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
   rc = op_sketch(h, P, p->k0 + k, ell, h->D);
   if (rc != NYS_OK) { stop(rc); return rc; }
   CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
@@ -881,17 +989,19 @@ int IpmRun::top() {
   ref_before = r->refine_steps;
 
   // Predictor (Algorithm 5, first step).
+  const BoxTerms bt = terms(false);
+  const BoxTerms* btp = box ? &bt : nullptr;
   if (lp) {
     int it = 0, ref = 0;
     rc = newton_lp(h, P, h->x, h->z, h->D, delta, h->r_d, h->r_p, h->r_xz, ell, eta, o.max_pcg_iter,
-                   h->dxp, h->dyp, h->dzp, &it, &ref);
+                   h->dxp, h->dyp, h->dzp, &it, &ref, btp);
     r->refine_steps += ref;
     req.rc = rc;
     req.iters = it;
     req.active = false;
     return NYS_OK;
   }
-  rc = newton_begin(h, m, n, A, lda, h->x, h->D, h->r_d, h->r_p, h->r_xz);
+  rc = newton_begin(h, m, n, A, lda, h->x, h->D, h->r_d, h->r_p, h->r_xz, btp);
   if (rc != NYS_OK) { stop(rc); return rc; }
   request(h->dyp);
   return NYS_OK;
@@ -902,34 +1012,43 @@ int IpmRun::top() {
 int IpmRun::mid() {
   const nys_options& o = h->opt;
   if (!take_request()) return status;
+  const BoxTerms btp_ = terms(false), btc_ = terms(true);
+  const BoxTerms* btp = box ? &btp_ : nullptr;
+  const BoxTerms* btc = box ? &btc_ : nullptr;
   if (!lp) {
-    const int rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, h->r_d, h->r_xz, h->dyp, h->dxp, h->dzp);
+    const int rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, h->r_d, h->r_xz, h->dyp, h->dxp, h->dzp, btp);
     if (rc != NYS_OK) { stop(rc); return rc; }
   }
-  CK(step_ratios_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, h->red_out, h->red));
+  if (box) CK(box_step_ratios_f64(h->st, n, h->vk, h->x, h->dxp, h->w, h->dwp, h->z, h->dzp, h->s, h->dsp,
+                                  h->red_out, h->red));
+  else CK(step_ratios_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, h->red_out, h->red));
   int rc = sync_scalars(h, 2);
   if (rc != NYS_OK) { stop(rc); return rc; }
   const double ap_bar = 0.995 * std::min(1.0, h->h_red[0]);
   const double ad_bar = 0.995 * std::min(1.0, h->h_red[1]);
-  CK(mu_aff_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, ap_bar, ad_bar, h->red_out, h->red));
+  if (box) CK(box_mu_aff_f64(h->st, n, h->vk, h->x, h->dxp, h->z, h->dzp, h->w, h->dwp, h->s, h->dsp, ap_bar,
+                             ad_bar, h->red_out, h->red));
+  else CK(mu_aff_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, ap_bar, ad_bar, h->red_out, h->red));
   rc = sync_scalars(h, 1);
   if (rc != NYS_OK) { stop(rc); return rc; }
-  const double mu_aff = h->h_red[0] / n;
-  const double mu_t = mu_aff * mu_aff * mu_aff / (mu * mu);
+  const double mu_aff = box ? (n_mu > 0.0 ? h->h_red[0] / n_mu : 0.0) : h->h_red[0] / n;
+  const double mu_t = mu > 0.0 ? mu_aff * mu_aff * mu_aff / (mu * mu) : 0.0;
 
-  // Corrector (Eq. corrector-RHS): r_d = r_p = 0, r_xz = mu_t - dxp dzp.
-  CK(corrector_rhs_f64(h->st, n, mu_t, h->dxp, h->dzp, h->r_xz));
+  // Corrector (Eq. corrector-RHS): r_d = r_p = 0 (and r_u = 0), r_xz = mu_t - dxp dzp
+  // (and r_ws = mu_t - dwp dsp).
+  if (box) CK(box_corrector_rhs_f64(h->st, n, h->vk, mu_t, h->dxp, h->dzp, h->dwp, h->dsp, h->r_xz, h->r_ws));
+  else CK(corrector_rhs_f64(h->st, n, mu_t, h->dxp, h->dzp, h->r_xz));
   if (lp) {
     int it = 0, ref = 0;
     rc = newton_lp(h, P, h->x, h->z, h->D, delta, nullptr, nullptr, h->r_xz, ell, eta, o.max_pcg_iter,
-                   h->dxc, h->dyc, h->dzc, &it, &ref);
+                   h->dxc, h->dyc, h->dzc, &it, &ref, btc);
     r->refine_steps += ref;
     req.rc = rc;
     req.iters = it;
     req.active = false;
     return NYS_OK;
   }
-  rc = newton_begin(h, m, n, A, lda, h->x, h->D, nullptr, nullptr, h->r_xz);
+  rc = newton_begin(h, m, n, A, lda, h->x, h->D, nullptr, nullptr, h->r_xz, btc);
   if (rc != NYS_OK) { stop(rc); return rc; }
   request(h->dyc);
   return NYS_OK;
@@ -938,17 +1057,28 @@ int IpmRun::mid() {
 // After the corrector's PCG: the combined direction and the step.
 int IpmRun::bottom() {
   if (!take_request()) return status;
+  const BoxTerms btc_ = terms(true);
   if (!lp) {
-    const int rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, nullptr, h->r_xz, h->dyc, h->dxc, h->dzc);
+    const int rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, nullptr, h->r_xz, h->dyc, h->dxc, h->dzc,
+                              box ? &btc_ : nullptr);
     if (rc != NYS_OK) { stop(rc); return rc; }
   }
   CK(add_dirs_f64(h->st, m, n, h->dxp, h->dyp, h->dzp, h->dxc, h->dyc, h->dzc));
-  CK(step_ratios_f64(h->st, n, h->x, h->dxc, h->z, h->dzc, h->red_out, h->red));
+  if (box) {
+    // (dw, ds) += (dwp, dsp): the same kernel over n-vectors only (m = 0)
+    CK(add_dirs_f64(h->st, 0, n, h->dwp, nullptr, h->dsp, h->dwc, nullptr, h->dsc));
+    CK(box_step_ratios_f64(h->st, n, h->vk, h->x, h->dxc, h->w, h->dwc, h->z, h->dzc, h->s, h->dsc, h->red_out,
+                           h->red));
+  } else {
+    CK(step_ratios_f64(h->st, n, h->x, h->dxc, h->z, h->dzc, h->red_out, h->red));
+  }
   const int rc = sync_scalars(h, 2);
   if (rc != NYS_OK) { stop(rc); return rc; }
   const double ap = 0.995 * std::min(1.0, h->h_red[0]);
   const double ad = 0.995 * std::min(1.0, h->h_red[1]);
   CK(ipm_update_f64(h->st, m, n, ap, ad, h->dxc, h->dyc, h->dzc, h->x, h->y, h->z));
+  // w moves with the primal step, s with the dual one
+  if (box) CK(ipm_update_f64(h->st, 0, n, ap, ad, h->dwc, nullptr, h->dsc, h->w, nullptr, h->s));
   if (h->trace) {
     cudaStreamSynchronize(h->st);
     const double t_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
@@ -971,10 +1101,13 @@ int IpmRun::finish() {
   CK(cudaMemcpyAsync(r->z, h->z, sizeof(double) * n, kout, h->st));
   if (r->lam) CK(cudaMemcpyAsync(r->lam, h->lam, sizeof(double) * m, kout, h->st));
   if (r->zeta) CK(cudaMemcpyAsync(r->zeta, h->zeta, sizeof(double) * n, kout, h->st));
+  if (box && r->w) CK(cudaMemcpyAsync(r->w, h->w, sizeof(double) * n, kout, h->st));
+  if (box && r->s) CK(cudaMemcpyAsync(r->s, h->s, sizeof(double) * n, kout, h->st));
   CK(objective_terms_f64(h->st, m, n, q, c, b, h->x, h->y, h->z, h->red_out + 4, h->red));
-  int rc2 = sync_scalars(h, 8);
+  if (box) CK(dot_f64(h->st, n, h->uv, h->s, h->red_out + 8, h->red));     // u^T s of (D~)
+  int rc2 = sync_scalars(h, box ? 9 : 8);
   const double xqx = h->h_red[4], cx = h->h_red[5], by = h->h_red[6];
-  const double pobj = 0.5 * xqx + cx, dobj = by - 0.5 * xqx;
+  const double pobj = 0.5 * xqx + cx, dobj = by - 0.5 * xqx - (box ? h->h_red[8] : 0.0);
   r->ipm_iters = k;
   r->rel_primal = rel_p;
   r->rel_dual = rel_d;
@@ -1533,6 +1666,8 @@ int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result*
     if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || P.a_dtype != NYS_F64 || P.host || !P.A || !P.q ||
         P.lda < n || !R.x || !R.y || !R.z)
       return fail(h, NYS_ERR_ARG, "nys_adjoint: problem %d is not a device FP64 problem of this handle", i);
+    if (P.var_kind)
+      return fail(h, NYS_ERR_ARG, "nys_adjoint: problem %d has free or box-constrained variables", i);
     const double* A = static_cast<const double*>(P.A);
     const int ell = std::min(h->ell_cap, m);
     const double* g = dL_dx + on;

@@ -55,7 +55,12 @@ class Problem(ctypes.Structure):
                 ("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("q", ctypes.c_void_p),
                 ("x0", ctypes.c_void_p), ("y0", ctypes.c_void_p), ("z0", ctypes.c_void_p),
                 ("host", ctypes.c_int), ("lam0", ctypes.c_void_p), ("zeta0", ctypes.c_void_p),
-                ("k0", ctypes.c_int), ("ell", ctypes.c_int)]
+                ("k0", ctypes.c_int), ("ell", ctypes.c_int),
+                ("var_kind", ctypes.c_void_p), ("u", ctypes.c_void_p), ("w0", ctypes.c_void_p),
+                ("s0", ctypes.c_void_p)]
+
+# variable kinds of problems (P~)/(D~) (Problem.var_kind)
+KIND_I, KIND_F, KIND_J = 0, 1, 2
 
 
 class Result(ctypes.Structure):
@@ -67,7 +72,7 @@ class Result(ctypes.Structure):
                 ("mu", ctypes.c_double), ("rel_gap", ctypes.c_double), ("rho", ctypes.c_double),
                 ("delta", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("pcg_seconds", ctypes.c_double), ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
-                ("pcg_log_len", ctypes.c_int)]
+                ("pcg_log_len", ctypes.c_int), ("w", ctypes.c_void_p), ("s", ctypes.c_void_p)]
 
 
 _lib = None
@@ -391,13 +396,34 @@ def nys_step_length(h: Handle, v, dv) -> float:
     return a.value
 
 
+def _box_fields(kind, u, s0, w0, n, dev, host):
+    """Problem fields of (P~)/(D~): int8 kinds, float64 u, s0 and optional w0 (n each)."""
+    if kind is None:
+        return {}, []
+    where = torch.device("cpu") if host else dev
+    if not isinstance(kind, torch.Tensor) or kind.dtype != torch.int8 or kind.shape != (n,) \
+            or not kind.is_contiguous() or kind.device != where:
+        raise TypeError(f"var_kind must be a contiguous int8 tensor of length {n} on {where}")
+    keep = [kind]
+    f = {"var_kind": kind.data_ptr()}
+    for t, nm in ((u, "u"), (s0, "s0"), (w0, "w0")):
+        if t is not None:
+            _f64(t, nm, where)
+            keep.append(t)
+            f[nm] = t.data_ptr()
+    return f, keep
+
+
 def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check: bool = True,
-              lam0=None, zeta0=None, k0: int = 0, want_pmm: bool = False):
+              lam0=None, zeta0=None, k0: int = 0, want_pmm: bool = False, kind=None, u=None,
+              s0=None, w0=None):
     """Solve one QP.  CUDA tensors -> device problem; CPU tensors -> host
     problem (the library stages the data; pin the tensors for fast copies).
     lam0/zeta0/k0 resume from a saved state (rho/delta come from the handle's
-    options).  Returns (x, y, z, info); with want_pmm, info also holds the
-    final lam and zeta."""
+    options).  kind (int8: KIND_I, KIND_F, KIND_J per variable), u, s0 and
+    optionally w0 make it problem (P~) with free and box-constrained
+    variables; info then also holds the final w and s.  Returns
+    (x, y, z, info); with want_pmm, info also holds the final lam and zeta."""
     m, n = A.shape
     host = not A.is_cuda
     dev = None if host else A.device
@@ -417,16 +443,19 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     for t, nm in ((lam0, "lam0"), (zeta0, "zeta0")):
         if t is not None:
             _f64(t, nm, dev if not host else torch.device("cpu"))
+    bf, _keep = _box_fields(kind, u, s0, w0, n, dev, host)
     p = Problem(m=m, n=n, a_dtype=a_dtype, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(),
                 c=c.data_ptr(), q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(),
                 z0=z0.data_ptr(), host=1 if host else 0,
                 lam0=lam0.data_ptr() if lam0 is not None else None,
-                zeta0=zeta0.data_ptr() if zeta0 is not None else None, k0=k0)
+                zeta0=zeta0.data_ptr() if zeta0 is not None else None, k0=k0, **bf)
     log = (ctypes.c_int * pcg_log_cap)()
+    w, s = (mk(n), mk(n)) if kind is not None else (None, None)
     r = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr(),
                lam=lam.data_ptr() if lam is not None else None,
                zeta=zeta.data_ptr() if zeta is not None else None,
-               pcg_log=log, pcg_log_cap=pcg_log_cap)
+               pcg_log=log, pcg_log_cap=pcg_log_cap,
+               w=w.data_ptr() if w is not None else None, s=s.data_ptr() if s is not None else None)
     rc = lib().nys_solve(h.h, ctypes.byref(p), ctypes.byref(r))
     if check:
         h.check(rc)
@@ -436,6 +465,8 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     info["pcg_log"] = list(log[: r.pcg_log_len])
     if want_pmm:
         info["lam"], info["zeta"] = lam, zeta
+    if kind is not None:
+        info["w"], info["s"] = w, s
     return x, y, z, info
 
 
@@ -484,32 +515,43 @@ def qp_solve(A, b, c, q, x0, y0, z0, handle, eta: float = 1e-12):
 
 
 def nys_solve_batched(h: Handle, problems, check: bool = True):
-    """Solve a list of QPs [(A, b, c, q, x0, y0, z0[, ell]), ...] (device
-    tensors; optional per-problem sketch size) in one call; the handle must
-    have max_batch >= 1.  Returns a list of (x, y, z, info)."""
+    """Solve a list of QPs [(A, b, c, q, x0, y0, z0[, ell[, box]]), ...]
+    (device tensors; optional per-problem sketch size, 0 = the handle's; box
+    = dict(kind=, u=, s0=[, w0=]) for a problem (P~)) in one call; the handle
+    must have max_batch >= 1.  Returns a list of (x, y, z, info); info holds
+    w and s for the (P~) problems."""
     k = len(problems)
     P = (Problem * k)()
     R = (Result * k)()
-    outs = []
+    outs, keep = [], []
     for i, pr in enumerate(problems):
         A, b, c, q, x0, y0, z0 = pr[:7]
         ell_i = int(pr[7]) if len(pr) > 7 else 0
+        bx = pr[8] if len(pr) > 8 else None
         m, n = A.shape
         a_dtype = NYS_F32 if A.dtype == torch.float32 else NYS_F64
         x = torch.empty(n, dtype=torch.float64, device=A.device)
         y = torch.empty(m, dtype=torch.float64, device=A.device)
         z = torch.empty(n, dtype=torch.float64, device=A.device)
+        bf, kp = _box_fields(bx.get("kind"), bx.get("u"), bx.get("s0"), bx.get("w0"), n, A.device, False) \
+            if bx else ({}, [])
+        keep += kp
+        w = torch.empty(n, dtype=torch.float64, device=A.device) if bx else None
+        s = torch.empty(n, dtype=torch.float64, device=A.device) if bx else None
         P[i] = Problem(m=m, n=n, a_dtype=a_dtype, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(), c=c.data_ptr(),
-                       q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(), z0=z0.data_ptr(), host=0, ell=ell_i)
-        R[i] = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr())
-        outs.append((x, y, z))
+                       q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(), z0=z0.data_ptr(), host=0, ell=ell_i, **bf)
+        R[i] = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr(),
+                      w=w.data_ptr() if w is not None else None, s=s.data_ptr() if s is not None else None)
+        outs.append((x, y, z, w, s))
     rc = lib().nys_solve_batched(h.h, k, P, R)
     if check:
         h.check(rc)
     res = []
-    for i, (x, y, z) in enumerate(outs):
+    for i, (x, y, z, w, s) in enumerate(outs):
         info = {f: getattr(R[i], f) for f in ("status", "ipm_iters", "pcg_iters_total", "refine_steps", "rel_primal",
                                               "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds",
                                               "pcg_seconds")}
+        if w is not None:
+            info["w"], info["s"] = w, s
         res.append((x, y, z, info))
     return res
