@@ -21,7 +21,8 @@ exact zeros, so both cases share one implementation.
 Pinning (tests/test_oracle_*.py): every function is checked against something
 other than itself -- the assembled 3x3-block Newton system (Eq. Newton) and
 the 5x5-block system with free and box-constrained variables
-(Eq. Newton-free-box), scipy's HiGHS on bounded LPs,
+(Eq. Newton-free-box), scipy's HiGHS on bounded LPs, hand-derived practical
+starting points (tests/golden/start_points.txt),
 P_Nys from Eq. Nys_precond against P_Nys^{-1} from Eq. Nys_precond_inv, the
 Nystrom invariants of Section 2.3.2, a dense direct solve of the normal
 equations, brute-force active-set solutions of tiny QPs, hand-derived KKT
@@ -588,6 +589,84 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     return Result(x=x, y=y, z=z, status=status, ipm_iters=k, pcg_iters=pcg_counts,
                   rel_p=rel_p, rel_d=rel_d, mu=mu, rel_gap=duality_gap(b, c, q, x, y, kind, u, s),
                   rho=rho, delta=delta, trace=trace, w=w, s=s)
+
+
+# ---------------------------------------------------------------------------
+# Practical initial point (the supplement's construction for the initial point,
+# after Mehrotra and Pougkakiotis-Gondzio).
+# ---------------------------------------------------------------------------
+
+START_DELTA = 10.0       # regularisation of A A^T in both candidate solves (supplement)
+START_PCG_TOL = 1e-10    # READING: relative residual of those two Nystrom PCG solves
+
+
+@dataclasses.dataclass
+class StartPoint:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    w: np.ndarray        # zero outside J
+    s: np.ndarray        # zero outside J
+    pcg_iters: tuple     # iterations of the two candidate solves
+
+
+def practical_start(A, b, c, q, opt: Options, kind=None, u=None, k: int = 0) -> StartPoint:
+    """Initial point of the supplement for (P~)/(D~) (problem (P) when kind is None).
+
+    Candidate: x~ = u/2 + A^T (A A^T)^{-1} (b - A u/2), y~ = (A A^T)^{-1} A (c + Q x~),
+    with A A^T regularised as A A^T + 10 I and both systems solved by Nystrom
+    PCG (Algorithm 1 on N = A A^T, i.e. D = I, with Omega_k; Algorithm 2 with
+    delta = 10); g = c - A^T y~ + Q x~; z~ = g/2 on J and g elsewhere;
+    s~_J = -z~_J; w~_J = u_J - x~_J.  Shifts: delta_p = max(-1.5 min over
+    x~_IJ and w~_J, 0), delta_d likewise over z~_IJ and s~_J;
+    gamma = (x~_IJ + delta_p)^T (z~_IJ + delta_d) + (w~_J + delta_p)^T (s~_J + delta_d);
+    delta_p~ = delta_p + gamma / 2 / (sum_IJ (z~ + delta_d) + sum_J (s~ + delta_d));
+    delta_d~ = delta_d + gamma / 2 / (sum_IJ (x~ + delta_p) + sum_J (w~ + delta_p)).
+    Start: x_IJ, w_J shifted by delta_p~ (x_F unshifted), z_IJ, s_J by
+    delta_d~, z_F = 0, y = y~.
+    READING: the supplement prints x~ + delta_d in the denominator of
+    delta_d~; the primal sums shifted by delta_p (the primal shift, as in
+    Mehrotra's heuristic) are used.  READING: Omega_k is the test matrix of
+    the first IPM iteration's index, and both PCG solves stop at the relative
+    residual START_PCG_TOL (or max_pcg_iter).  A shift whose denominator is 0
+    (no bounded variable) is 0."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    kind = np.zeros(n, dtype=np.int8) if kind is None else np.asarray(kind, dtype=np.int8)
+    ij, jj = kind != KIND_F, kind == KIND_J
+    uu = np.zeros(n) if u is None else np.where(jj, np.asarray(u, dtype=np.float64), 0.0)
+    ones = np.ones(n)
+    F = nystrom(A, ones, gaussian_omega(opt.seed, k, m, min(opt.ell, m)))
+    apply_M = lambda v: normal_matvec(A, ones, START_DELTA, v)
+    apply_P = lambda v: precond_inv_apply(F, START_DELTA, v)
+    r1 = pcg(apply_M, apply_P, b - A @ (0.5 * uu), START_PCG_TOL, opt.max_pcg_iter)
+    xt = 0.5 * uu + A.T @ r1.x
+    r2 = pcg(apply_M, apply_P, A @ (c + q * xt), START_PCG_TOL, opt.max_pcg_iter)
+    yt = r2.x
+    g = c - A.T @ yt + q * xt
+    zt = np.where(jj, 0.5 * g, g)
+    st = np.where(jj, -zt, 0.0)
+    wt = np.where(jj, uu - xt, 0.0)
+    prim = np.concatenate([xt[ij], wt[jj]])
+    dual = np.concatenate([zt[ij], st[jj]])
+    dp = max(-1.5 * float(np.min(prim)), 0.0) if prim.size else 0.0
+    dd = max(-1.5 * float(np.min(dual)), 0.0) if dual.size else 0.0
+    gamma = float((xt[ij] + dp) @ (zt[ij] + dd)) + float((wt[jj] + dp) @ (st[jj] + dd))
+    den_p = float(np.sum(zt[ij] + dd)) + float(np.sum(st[jj] + dd))
+    den_d = float(np.sum(xt[ij] + dp)) + float(np.sum(wt[jj] + dp))
+    dpt = dp + (0.5 * gamma / den_p if den_p != 0.0 else 0.0)
+    ddt = dd + (0.5 * gamma / den_d if den_d != 0.0 else 0.0)
+    return StartPoint(x=np.where(ij, xt + dpt, xt), y=yt, z=np.where(ij, zt + ddt, 0.0),
+                      w=np.where(jj, wt + dpt, 0.0), s=np.where(jj, st + ddt, 0.0),
+                      pcg_iters=(r1.iters, r2.iters))
+
+
+def solve_from_practical_start(A, b, c, q, opt: Options, kind=None, u=None, k0: int = 0, **kw) -> Result:
+    """Algorithm 6 started at practical_start() (Omega_{k0} for its sketch)."""
+    st = practical_start(A, b, c, q, opt, kind, u, k0)
+    if kind is None:
+        return solve(A, b, c, q, st.x, st.y, st.z, opt, k0=k0, **kw)
+    return solve(A, b, c, q, st.x, st.y, st.z, opt, k0=k0, kind=kind, u=u, s0=st.s, w0=st.w, **kw)
 
 
 def solve_qp(qp, opt: Options, **kw) -> Result:

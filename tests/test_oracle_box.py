@@ -341,3 +341,71 @@ def test_box_iteration_equals_standard_form_with_explicit_slacks(seed):
     assert close(rb.z, re.z[:n]) and close(rb.s[J], re.z[n:])
     assert abs(rb.trace[0].alpha_p - re.trace[0].alpha_p) < 1e-10
     assert abs(rb.trace[0].alpha_d - re.trace[0].alpha_d) < 1e-10
+
+
+# ------------------------------------------------------------ practical start
+
+def _read_start_golden():
+    recs = []
+    with open(os.path.join(GOLDEN, "start_points.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            p = [t.strip() for t in line.split("|")]
+            vec = lambda t: np.array([float(v) for v in t.split()])
+            A = np.array([[float(v) for v in row.split()] for row in p[3].split(";")])
+            recs.append(dict(name=p[0], kind=_kinds(p[1]), u=vec(p[2]), A=A, b=vec(p[4]), c=vec(p[5]),
+                             q=vec(p[6]), x=vec(p[7]), y=vec(p[8]), z=vec(p[9]), w=vec(p[10]), s=vec(p[11])))
+    return recs
+
+
+@pytest.mark.parametrize("rec", _read_start_golden(), ids=lambda r: r["name"])
+def test_practical_start_matches_hand_derived_points(rec):
+    st = O.practical_start(rec["A"], rec["b"], rec["c"], rec["q"], O.Options(ell=1, seed=0), rec["kind"], rec["u"])
+    for got, nm in ((st.x, "x"), (st.y, "y"), (st.z, "z"), (st.w, "w"), (st.s, "s")):
+        assert np.allclose(got, rec[nm], rtol=1e-12, atol=1e-12), nm
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_practical_start_is_strictly_interior(seed):
+    """Whatever the candidate's signs, the shifted start has x_IJ, z_IJ, w_J,
+    s_J > 0, z_F = 0 and w = s = 0 outside J (the purpose of the shifts)."""
+    qp = synth.box_qp(900 + seed, 30, 90, 0.2, 0.4)
+    c = qp.c + 3.0 * np.random.default_rng(seed).standard_normal(qp.n)     # far from dual feasible
+    st = O.practical_start(qp.A, qp.b, c, qp.q, O.Options(ell=8, seed=seed), qp.kind, qp.u)
+    ij, jj = qp.kind != KF, qp.kind == KJ
+    assert np.all(st.x[ij] > 0) and np.all(st.z[ij] > 0) and np.all(st.w[jj] > 0) and np.all(st.s[jj] > 0)
+    assert np.all(st.z[~ij] == 0) and np.all(st.w[~jj] == 0) and np.all(st.s[~jj] == 0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_solve_from_practical_start_matches_active_set_enumeration(seed):
+    """From the practical start (no interior point supplied) the solve reaches
+    the brute-force optimum of a tiny QP with free, non-negative and box
+    variables."""
+    rng = np.random.default_rng(700 + seed)
+    m, n = 2, 7
+    A = rng.standard_normal((m, n))
+    kind = np.array([KF, KI, KI, KJ, KJ, KJ, KI], dtype=np.int8)
+    x0 = np.where(kind == KF, rng.standard_normal(n), rng.uniform(0.5, 1.5, n))
+    u = np.where(kind == KJ, x0 + rng.uniform(0.1, 0.6, n), 0.0)
+    b = A @ x0
+    c = 2.0 * rng.standard_normal(n)
+    q = rng.uniform(0.2, 1.0, n)
+    xs, ys, _, _ = _box_active_set_brute_force(A, b, c, q, kind, u)
+    r = O.solve_from_practical_start(A, b, c, q, O.Options(tol=1e-10, ell=2, seed=seed), kind, u)
+    assert r.status == "converged"
+    assert np.allclose(r.x, xs, atol=1e-6) and np.allclose(r.y, ys, atol=1e-5)
+
+
+def test_solve_from_practical_start_reaches_the_same_solution():
+    """The 200 x 500 workloads, (P) and (P~), from the practical start instead
+    of the generator's interior point: converged, and the same optimum (the
+    QPs are strictly convex where q > 0 and have a unique solution)."""
+    for qp in (synth.workload_small(), synth.workload_box()):
+        opt = O.Options(tol=1e-8, ell=20, seed=7)
+        a = O.solve_qp(qp, opt)
+        b = O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
+        assert a.status == "converged" and b.status == "converged" and b.ipm_iters < 60
+        assert np.linalg.norm(a.x - b.x) <= 1e-5 * np.linalg.norm(a.x)
