@@ -205,7 +205,7 @@ def oracle_component_times(A64, b, c, q, x0, y0, z0, ell, tol, seed, box=None):
     return t_ipm, (time.perf_counter() - t0) / k
 
 
-def cpu_baseline(problems, w, runs, seed):
+def cpu_baseline(problems, w, runs, seed, practical=False):
     """The oracle as it stands on this host's cores: a whole solve when one
     takes at most ~30 s (else timed components extrapolated with the GPU
     run's iteration counts)."""
@@ -221,8 +221,12 @@ def cpu_baseline(problems, w, runs, seed):
     if est * per_step <= 30.0:
         t0 = time.perf_counter()
         for p in problems:
-            O.solve(p["A64"], p["b"], p["c"], p["q"], p["x0"], p["y0"], p["z0"],
-                    O.Options(tol=w["tol"], ell=p["ell"], seed=seed), **(p.get("box") or {}))
+            opt = O.Options(tol=w["tol"], ell=p["ell"], seed=seed)
+            if practical:
+                bx = p.get("box") or {}
+                O.solve_from_practical_start(p["A64"], p["b"], p["c"], p["q"], opt, bx.get("kind"), bx.get("u"))
+            else:
+                O.solve(p["A64"], p["b"], p["c"], p["q"], p["x0"], p["y0"], p["z0"], opt, **(p.get("box") or {}))
         full = time.perf_counter() - t0
         return {"value": per_step / full / per_step, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
                 "sample": f"whole oracle solve(s) of the same workload ({per_step} QP, {full:.2f} s)"}
@@ -286,6 +290,9 @@ def main():
                     help="generate the large precision workloads with numpy instead of on the GPU")
     ap.add_argument("--no-gemv", action="store_true",
                     help="skip the operator GEMV measurement at the large workload shapes")
+    ap.add_argument("--practical-start", action="store_true",
+                    help="start every solve at the practical initial point (start_mode=1) instead of the "
+                         "workload's interior point")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision workloads: also time one FP64-form solve of the same QP")
     ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm", "ff_pcg", "bf16_pcg"],
@@ -343,14 +350,17 @@ def main():
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=32, stream=stream)
         else:
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream,
-                           precision_mode={"bf16": 1, "fp8": 2}.get(form, 0))
+                           precision_mode={"bf16": 1, "fp8": 2}.get(form, 0),
+                           start_mode=1 if args.practical_start else 0)
+        # the start point the solves receive (None: the practical start computes it)
+        start = (lambda pr: pr[4:7]) if not args.practical_start else (lambda pr: (None, None, None))
 
         def step():
             if form == "batch":
                 return [r[3] for r in nys.nys_solve_batched(h, dev_probs)]
             out = []
             for pr in dev_probs:
-                x, y, z, info = nys.nys_solve(h, *pr[:7], **(pr[8] if len(pr) > 8 else {}))
+                x, y, z, info = nys.nys_solve(h, *pr[:4], *start(pr), **(pr[8] if len(pr) > 8 else {}))
                 if form == "diff":
                     g = 2.0 * (x - T(host_probs[len(out)].target))
                     nys.nys_adjoint(h, pr[0], pr[3], x, y, z, info, g, eta=1e-10)
@@ -437,8 +447,10 @@ def main():
         e2e = None
         if form in ("fp64", "box", "bf16", "fp8"):
             pin = lambda t: t.detach().cpu().pin_memory()
-            hp = [tuple(pin(t) for t in pr[:7]) for pr in dev_probs]
-            hbox = [{k: pin(t) for k, t in pr[8].items()} if len(pr) > 8 else {} for pr in dev_probs]
+            hp = [tuple(pin(t) for t in pr[:4]) + tuple(None if t is None else pin(t) for t in start(pr))
+                  for pr in dev_probs]
+            hbox = [{k: pin(t) for k, t in pr[8].items() if not (args.practical_start and k in ("s0", "w0"))}
+                    if len(pr) > 8 else {} for pr in dev_probs]
             nys.nys_solve(h, *hp[0], **hbox[0])
             barrier()
             t0 = time.perf_counter()
@@ -450,7 +462,7 @@ def main():
                 te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
                 dist.all_reduce(te, op=dist.ReduceOp.MAX)
                 e2e_s = float(te[0])
-            h2d = sum(sum(t.numel() * t.element_size() for t in pr) for pr in hp) + \
+            h2d = sum(sum(t.numel() * t.element_size() for t in pr if t is not None) for pr in hp) + \
                 sum(sum(t.numel() * t.element_size() for t in bx.values()) for bx in hbox)
             d2h = sum(8 * (2 * pr[0].shape[1] + pr[0].shape[0]) for pr in hp) + \
                 sum(8 * 2 * pr[0].shape[1] for pr, bx in zip(hp, hbox) if bx)
@@ -491,7 +503,7 @@ def main():
                 probs.append(dict(A64=pr[0].double().cpu().numpy(), b=pr[1].cpu().numpy(), c=pr[2].cpu().numpy(),
                                   q=pr[3].cpu().numpy(), x0=pr[4].cpu().numpy(), y0=pr[5].cpu().numpy(),
                                   z0=pr[6].cpu().numpy(), ell=pr[7]))
-            cpu = cpu_baseline(probs, w, runs, seed)
+            cpu = cpu_baseline(probs, w, runs, seed, args.practical_start)
         line = {
             "metric": "QP solves/s to KKT tol", "value": value, "unit": "QP solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -500,6 +512,7 @@ def main():
                       "diff": "f64"}[form],
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
+                       "start": "practical initial point" if args.practical_start else "workload interior point",
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6
                        else f"A = {a_bytes / 1e6:.1f} MB fits in L2 (no flush; latency-bound)"},

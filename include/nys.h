@@ -68,6 +68,17 @@ typedef struct {
     const int* forced_pcg_iters;
     int n_forced_pcg;
     int forced_ipm_iters;
+    /* Start point: 0 = the problem's x0, y0, z0 (and w0, s0); 1 = the
+     * practical initial point of the supplement's construction: candidate
+     * x~ = u/2 + A^T (A A^T + 10 I)^{-1} (b - A u/2) and
+     * y~ = (A A^T + 10 I)^{-1} A (c + Q x~), both by Nystrom PCG on A A^T
+     * (Omega of the first IPM iteration, relative residual 1e-10; not counted
+     * in pcg_iters_total / pcg_log), z~ = c - A^T y~ + Q x~ (halved on J),
+     * s~_J = -z~_J, w~_J = u_J - x~_J, then the shifts that make x, w, z, s
+     * strictly positive (the denominator of the dual shift sums x~ + delta_p:
+     * the printed x~ + delta_d is read as the primal shift).  With 1 the
+     * problem's x0, y0, z0, w0, s0 are ignored and may be NULL. */
+    int start_mode;
 } nys_options;
 
 /* One QP.  With host == 0 all pointers are device pointers; with host == 1

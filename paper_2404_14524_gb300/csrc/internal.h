@@ -282,10 +282,12 @@ struct BoxVectors {
   const double* s = nullptr;
 };
 // In place on the handle's copies: z_F = 0; on J w = w0 (has_w0) or u - x,
-// s = s0; elsewhere u = w = s = 0.  out[0] = |I u J| + |J|, out[1] = ||u_J||^2,
-// out[2] = count of invalid entries (device).
+// s = s0 (only when given_start: the practical start writes w, s on J
+// itself); elsewhere u = w = s = 0.  out[0] = |I u J| + |J|,
+// out[1] = ||u_J||^2, out[2] = count of invalid entries (device).
 cudaError_t box_start_f64(cudaStream_t st, int n, const signed char* vk, double* u, const double* x, double* z,
-                          double* w, double* s, int has_u, int has_w0, int has_s0, double* out, RedBuf red);
+                          double* w, double* s, int has_u, int has_w0, int has_s0, int given_start, double* out,
+                          RedBuf red);
 // D = 1 / (q + Theta^{-1} + rho), Theta^{-1} = z/x on I, z/x + s/w on J, 0 on F
 cudaError_t box_scaling_f64(cudaStream_t st, int n, const signed char* vk, const double* x, const double* z,
                             const double* w, const double* s, const double* q, double rho, double* D);
@@ -316,6 +318,21 @@ cudaError_t box_mu_aff_f64(cudaStream_t st, int n, const signed char* vk, const 
 cudaError_t box_corrector_rhs_f64(cudaStream_t st, int n, const signed char* vk, double mu_t, const double* dxp,
                                   const double* dzp, const double* dwp, const double* dsp, double* r_xz,
                                   double* r_ws);
+// ---------------------------------------------------------------- practical initial point
+// out[0..len) = v
+cudaError_t fill_f64(cudaStream_t st, int len, double v, double* out);
+// candidate z~ (g/2 on J, 0 on F), w~ = u - x~ and s~ = -z~ on J from g = c - A^T y~ + Q x~;
+// out[0] = min over x~_IJ, w~_J; out[1] = min over z~_IJ, s~_J (device; +inf if empty).
+// vk null: problem (P), w and s untouched.
+cudaError_t start_candidate_f64(cudaStream_t st, int n, const signed char* vk, const double* c, const double* q,
+                                const double* u, const double* x, const double* Aty, double* z, double* w,
+                                double* s, double* out, RedBuf red);
+// out[0] = gamma, out[1] = sum (z~ + dd, s~ + dd), out[2] = sum (x~ + dp, w~ + dp) (device)
+cudaError_t start_sums_f64(cudaStream_t st, int n, const signed char* vk, const double* x, const double* z,
+                           const double* w, const double* s, double dp, double dd, double* out, RedBuf red);
+// x_IJ, w_J += dpt; z_IJ, s_J += ddt
+cudaError_t start_shift_f64(cudaStream_t st, int n, const signed char* vk, double dpt, double ddt, double* x,
+                            double* z, double* w, double* s);
 // out = a .* b
 cudaError_t vmul_f64(cudaStream_t st, int len, const double* a, const double* b, double* out);
 // out[i, j] = alpha u_i v_j + beta w_i s_j, row-major m x n (FP32 or FP64 out)

@@ -25,16 +25,17 @@ int grid_for(long long len) {
   return b < 1 ? 1 : (int)b;
 }
 
-// Start of a (P~) solve, in place on the handle's copies: z_F = 0; on J the
-// slack w = w0 (or u - x0) and s = s0, elsewhere u = w = s = 0.
+// Start of a (P~) solve, in place on the handle's copies: z_F = 0; on J,
+// for a given start, the slack w = w0 (or u - x0) and s = s0 (the practical
+// start writes w and s on J itself); elsewhere u = w = s = 0.
 // out[0] = |I u J| + |J| (the divisor of mu), out[1] = ||u_J||^2,
-// out[2] = number of invalid entries (kind outside {I, F, J}; on J a
-// non-finite u, or w <= 0, or s <= 0, or u or s0 missing).
+// out[2] = number of invalid entries (kind outside {I, F, J}; on J a missing
+// or non-finite u, and for a given start w <= 0, s <= 0 or s0 missing).
 __global__ void __launch_bounds__(kNT) k_box_start(int n, const signed char* __restrict__ vk, double* __restrict__ u,
                                                    const double* __restrict__ x, double* __restrict__ z,
                                                    double* __restrict__ w, double* __restrict__ s, int has_u,
-                                                   int has_w0, int has_s0, double* out, double* part,
-                                                   unsigned* cnt) {
+                                                   int has_w0, int has_s0, int given_start, double* out,
+                                                   double* part, unsigned* cnt) {
   double v[3] = {0.0, 0.0, 0.0};
   for (int j = blockIdx.x * kNT + threadIdx.x; j < n; j += gridDim.x * kNT) {
     const signed char k = vk[j];
@@ -44,17 +45,20 @@ __global__ void __launch_bounds__(kNT) k_box_start(int n, const signed char* __r
     }
     if (k == kF) z[j] = 0.0;
     if (k == kJ) {
-      if (!has_u || !has_s0) {
+      if (!has_u || (given_start && !has_s0)) {
         v[2] += 1.0;
         continue;
       }
       const double uj = u[j];
-      const double wj = has_w0 ? w[j] : uj - x[j];
-      w[j] = wj;
-      if (!isfinite(uj) || !(wj > 0.0) || !(s[j] > 0.0)) v[2] += 1.0;
+      if (!isfinite(uj)) v[2] += 1.0;
+      if (given_start) {
+        const double wj = has_w0 ? w[j] : uj - x[j];
+        w[j] = wj;
+        if (!(wj > 0.0) || !(s[j] > 0.0)) v[2] += 1.0;
+      }
       v[1] = fma(uj, uj, v[1]);
     } else {
-      if (has_u) u[j] = 0.0;
+      u[j] = 0.0;
       w[j] = 0.0;
       s[j] = 0.0;
     }
@@ -229,9 +233,10 @@ __global__ void k_box_corrector_rhs(int n, const signed char* __restrict__ vk, d
 }  // namespace
 
 cudaError_t box_start_f64(cudaStream_t st, int n, const signed char* vk, double* u, const double* x, double* z,
-                          double* w, double* s, int has_u, int has_w0, int has_s0, double* out, RedBuf red) {
+                          double* w, double* s, int has_u, int has_w0, int has_s0, int given_start, double* out,
+                          RedBuf red) {
   count_launches(1);
-  k_box_start<<<grid_for(n), kNT, 0, st>>>(n, vk, u, x, z, w, s, has_u, has_w0, has_s0, out, red.part,
+  k_box_start<<<grid_for(n), kNT, 0, st>>>(n, vk, u, x, z, w, s, has_u, has_w0, has_s0, given_start, out, red.part,
                                            red.cnt + 11);
   return cudaGetLastError();
 }

@@ -795,6 +795,9 @@ struct IpmRun {
   }
   // residuals of Eq. predictor-RHS at the current iterate and PMM parameters
   int residuals();
+  // the practical initial point into h->x, y, z (and w, s)
+  int practical_start();
+  int start_pcg(const double* rhs, double* out);
   int start(nys_solver* h_, const nys_problem* p_, nys_result* r_);
   int top();
   int mid();
@@ -809,9 +812,11 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   m = p->m; n = p->n;
   const nys_options& o = h->opt;
   lp = o.precision_mode >= 1;
+  const bool given = o.start_mode == 0;
   if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || p->lda < n ||
-      p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q || !p->x0 || !p->y0 ||
-      !p->z0 || !r->x || !r->y || !r->z || p->k0 < 0 || p->ell < 0) {
+      p->a_dtype != (lp ? NYS_F32 : NYS_F64) || !p->A || !p->b || !p->c || !p->q ||
+      (given && (!p->x0 || !p->y0 || !p->z0)) || (o.start_mode != 0 && o.start_mode != 1) ||
+      !r->x || !r->y || !r->z || p->k0 < 0 || p->ell < 0) {
     done = true;
     return status = fail(h, NYS_ERR_ARG,
                          "nys_solve: bad problem (sizes, dtype for the precision mode, or null pointers)");
@@ -866,13 +871,11 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
     CK(quantize_fp8(h->st, m, n, static_cast<const float*>(Av), lda, h->rs32, h->rs64, h->A8, h->ld_q, h->A8T,
                     h->ld_qt));
   const cudaMemcpyKind kin = p->host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  CK(cudaMemcpyAsync(h->x, p->x0, sizeof(double) * n, kin, h->st));
-  CK(cudaMemcpyAsync(h->y, p->y0, sizeof(double) * m, kin, h->st));
-  CK(cudaMemcpyAsync(h->z, p->z0, sizeof(double) * n, kin, h->st));
-  if (p->lam0) CK(cudaMemcpyAsync(h->lam, p->lam0, sizeof(double) * m, kin, h->st));
-  else CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
-  if (p->zeta0) CK(cudaMemcpyAsync(h->zeta, p->zeta0, sizeof(double) * n, kin, h->st));
-  else CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  if (given) {
+    CK(cudaMemcpyAsync(h->x, p->x0, sizeof(double) * n, kin, h->st));
+    CK(cudaMemcpyAsync(h->y, p->y0, sizeof(double) * m, kin, h->st));
+    CK(cudaMemcpyAsync(h->z, p->z0, sizeof(double) * n, kin, h->st));
+  }
   CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
   box = p->var_kind != nullptr;
   if (box) {
@@ -881,11 +884,11 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
     CK(cudaMemcpyAsync(h->vk, p->var_kind, (size_t)n, kin, h->st));
     if (p->u) CK(cudaMemcpyAsync(h->uv, p->u, sizeof(double) * n, kin, h->st));
     else CK(cudaMemsetAsync(h->uv, 0, sizeof(double) * n, h->st));
-    if (p->w0) CK(cudaMemcpyAsync(h->w, p->w0, sizeof(double) * n, kin, h->st));
-    if (p->s0) CK(cudaMemcpyAsync(h->s, p->s0, sizeof(double) * n, kin, h->st));
+    if (given && p->w0) CK(cudaMemcpyAsync(h->w, p->w0, sizeof(double) * n, kin, h->st));
+    if (given && p->s0) CK(cudaMemcpyAsync(h->s, p->s0, sizeof(double) * n, kin, h->st));
     else CK(cudaMemsetAsync(h->s, 0, sizeof(double) * n, h->st));
-    CK(box_start_f64(h->st, n, h->vk, h->uv, h->x, h->z, h->w, h->s, p->u != nullptr, p->w0 != nullptr,
-                     p->s0 != nullptr, h->red_out + 10, h->red));
+    CK(box_start_f64(h->st, n, h->vk, h->uv, h->x, h->z, h->w, h->s, p->u != nullptr, given && p->w0 != nullptr,
+                     given && p->s0 != nullptr, given ? 1 : 0, h->red_out + 10, h->red));
   }
   CK(dot_f64(h->st, m, b, b, h->red_out + 8, h->red));
   CK(dot_f64(h->st, n, c, c, h->red_out + 9, h->red));
@@ -903,11 +906,98 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
     n_mu = h->h_red[10];
     pnorm = std::sqrt(h->h_red[8] + h->h_red[11]);
   }
+  if (!given) {
+    rc = practical_start();
+    if (rc < 0) return r->status = status = rc;
+    if (rc > 0) warn = rc;
+  }
+  if (p->lam0) CK(cudaMemcpyAsync(h->lam, p->lam0, sizeof(double) * m, kin, h->st));
+  else CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  if (p->zeta0) CK(cudaMemcpyAsync(h->zeta, p->zeta0, sizeof(double) * n, kin, h->st));
+  else CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   rho = o.rho0;
   delta = o.delta0;
   status = NYS_WARN_MAXITER;
   done = false;
   return NYS_OK;
+}
+
+// One of the practical start's two solves: (A A^T + 10 I) out = rhs by Nystrom
+// PCG with the factor in h->U, h->lamh (D = h->D = 1), to relative residual
+// 1e-10; the FP64 route for the FP64 form, the FP32 matrix with float-float
+// sums for the precision form.
+int IpmRun::start_pcg(const double* rhs, double* out) {
+  constexpr double kStartDelta = 10.0, kStartTol = 1e-10;
+  int it = 0;
+  if (!lp)
+    return run_pcg(h, m, n, A, lda, h->D, kStartDelta, ell, h->U, h->ld, h->lamh, rhs, out, kStartTol,
+                   h->opt.max_pcg_iter, -1, &it);
+  CK(to_f32(h->st, n, (int)align_up(n, 8), h->D, nullptr, h->Df));
+  OpSpec op{};
+  op.kind = 3;
+  op.lp = make_lp_op(h, P, 3, h->D);
+  return run_pcg(h, m, n, op, kStartDelta, ell, h->U, h->ld, h->lamh, rhs, out, kStartTol, h->opt.max_pcg_iter, -1,
+                 &it);
+}
+
+// The practical initial point (the supplement's construction): candidate
+// x~ = u/2 + A^T v with (A A^T + 10 I) v = b - A u/2, y~ from
+// (A A^T + 10 I) y~ = A (c + Q x~), the candidate's z~, w~, s~, and the shifts
+// delta_p~, delta_d~ that make x_IJ, w_J, z_IJ, s_J strictly positive.
+int IpmRun::practical_start() {
+  const signed char* vk = box ? h->vk : nullptr;
+  // Nystrom factor of N = A A^T (D = 1) from Omega_{k0}
+  CK(fill_f64(h->st, n, 1.0, h->D));
+  int rc = op_sketch(h, P, p->k0, ell, h->D);
+  if (rc != NYS_OK) return rc;
+  CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red, h->cw,
+                      h->num_sms));
+  int warn_ = NYS_OK;
+  // x~ = u/2 + A^T v,  (A A^T + 10 I) v = b - A u/2
+  if (box) {
+    CK(axpby_f64(h->st, n, 0.5, h->uv, 0.0, h->uv, h->t_n));
+    rc = op_Ax(h, P, h->t_n, 0.0, nullptr, h->Ax);
+    if (rc != NYS_OK) return rc;
+    CK(axpby_f64(h->st, m, 1.0, b, -1.0, h->Ax, h->xi));
+  } else {
+    CK(cudaMemcpyAsync(h->xi, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  }
+  rc = start_pcg(h->xi, h->dyp);
+  if (rc < 0) return rc;
+  if (rc > 0) warn_ = rc;
+  rc = op_Aty(h, P, h->dyp, nullptr, h->g_n);
+  if (rc != NYS_OK) return rc;
+  if (box) CK(axpby_f64(h->st, n, 0.5, h->uv, 1.0, h->g_n, h->x));
+  else CK(cudaMemcpyAsync(h->x, h->g_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+  // y~:  (A A^T + 10 I) y~ = A (c + Q x~)
+  CK(vmul_f64(h->st, n, q, h->x, h->t_n));
+  CK(axpby_f64(h->st, n, 1.0, c, 1.0, h->t_n, h->t_n));
+  rc = op_Ax(h, P, h->t_n, 0.0, nullptr, h->xi);
+  if (rc != NYS_OK) return rc;
+  rc = start_pcg(h->xi, h->y);
+  if (rc < 0) return rc;
+  if (rc > 0) warn_ = rc;
+  rc = op_Aty(h, P, h->y, nullptr, h->Aty);
+  if (rc != NYS_OK) return rc;
+  // candidate z~, w~, s~ and the smallest primal / dual entries
+  CK(start_candidate_f64(h->st, n, vk, c, q, h->uv, h->x, h->Aty, h->z, box ? h->w : nullptr,
+                         box ? h->s : nullptr, h->red_out, h->red));
+  rc = sync_scalars(h, 2);
+  if (rc != NYS_OK) return rc;
+  const double pmin = h->h_red[0], dmin = h->h_red[1];
+  const double dp = std::isfinite(pmin) ? std::max(-1.5 * pmin, 0.0) : 0.0;
+  const double dd = std::isfinite(dmin) ? std::max(-1.5 * dmin, 0.0) : 0.0;
+  CK(start_sums_f64(h->st, n, vk, h->x, h->z, box ? h->w : nullptr, box ? h->s : nullptr, dp, dd, h->red_out,
+                    h->red));
+  rc = sync_scalars(h, 3);
+  if (rc != NYS_OK) return rc;
+  const double gamma = h->h_red[0], den_p = h->h_red[1], den_d = h->h_red[2];
+  if (!std::isfinite(gamma) || !std::isfinite(den_p) || !std::isfinite(den_d))
+    return fail(h, NYS_ERR_NUMERIC, "nys_solve: non-finite practical start");
+  const double dpt = dp + (den_p != 0.0 ? 0.5 * gamma / den_p : 0.0);
+  const double ddt = dd + (den_d != 0.0 ? 0.5 * gamma / den_d : 0.0);
+  CK(start_shift_f64(h->st, n, vk, dpt, ddt, h->x, h->z, box ? h->w : nullptr, box ? h->s : nullptr));
+  return warn_;
 }
 
 // Eq. predictor-RHS at the current iterate: r_d, r_p, r_xz (and r_u, r_ws).
@@ -1278,6 +1368,7 @@ void nys_default_options(nys_options* o) {
   o->forced_pcg_iters = nullptr;
   o->n_forced_pcg = 0;
   o->forced_ipm_iters = -1;
+  o->start_mode = 0;
 }
 
 const char* nys_last_error(nys_handle h) { return h ? h->err.c_str() : "null handle"; }

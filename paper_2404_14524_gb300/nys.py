@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("precision_mode", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("reg_floor", ctypes.c_double),
                 ("forced_pcg_iters", ctypes.POINTER(ctypes.c_int)), ("n_forced_pcg", ctypes.c_int),
-                ("forced_ipm_iters", ctypes.c_int)]
+                ("forced_ipm_iters", ctypes.c_int), ("start_mode", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -422,7 +422,9 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     lam0/zeta0/k0 resume from a saved state (rho/delta come from the handle's
     options).  kind (int8: KIND_I, KIND_F, KIND_J per variable), u, s0 and
     optionally w0 make it problem (P~) with free and box-constrained
-    variables; info then also holds the final w and s.  Returns
+    variables; info then also holds the final w and s.  With a handle
+    created with start_mode=1 (the practical initial point) x0, y0, z0, s0
+    and w0 may be None.  Returns
     (x, y, z, info); with want_pmm, info also holds the final lam and zeta."""
     m, n = A.shape
     host = not A.is_cuda
@@ -435,7 +437,8 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
         a_dtype = NYS_F64
         _f64(A, "A", dev if not host else torch.device("cpu"))
     for t, nm in ((b, "b"), (c, "c"), (q, "q"), (x0, "x0"), (y0, "y0"), (z0, "z0")):
-        _f64(t, nm, dev if not host else torch.device("cpu"))
+        if t is not None or nm in ("b", "c", "q"):       # x0, y0, z0 may be None with start_mode=1
+            _f64(t, nm, dev if not host else torch.device("cpu"))
     mk = (lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True)) if host else \
         (lambda k: torch.empty(k, dtype=torch.float64, device=dev))
     x, y, z = mk(n), mk(m), mk(n)
@@ -444,9 +447,10 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
         if t is not None:
             _f64(t, nm, dev if not host else torch.device("cpu"))
     bf, _keep = _box_fields(kind, u, s0, w0, n, dev, host)
+    opt_ptr = lambda t: t.data_ptr() if t is not None else None
     p = Problem(m=m, n=n, a_dtype=a_dtype, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(),
-                c=c.data_ptr(), q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(),
-                z0=z0.data_ptr(), host=1 if host else 0,
+                c=c.data_ptr(), q=q.data_ptr(), x0=opt_ptr(x0), y0=opt_ptr(y0),
+                z0=opt_ptr(z0), host=1 if host else 0,
                 lam0=lam0.data_ptr() if lam0 is not None else None,
                 zeta0=zeta0.data_ptr() if zeta0 is not None else None, k0=k0, **bf)
     log = (ctypes.c_int * pcg_log_cap)()

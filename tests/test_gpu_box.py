@@ -280,3 +280,59 @@ def test_box_precision_form_meets_kkt(nys):
     rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, *_np(x, y, z), qp.kind, qp.u, *_np(info["w"], info["s"]))
     assert rp <= 1e-6 and rd <= 1e-6 and mu <= 1e-6
     assert relerr(x, ref.x) <= 1e-3
+
+
+# ------------------------------------------------------------ practical start
+
+@pytest.mark.parametrize("which", ["plain", "box"])
+def test_practical_start_matches_oracle(nys, which):
+    """start_mode=1 with zero IPM iterations returns the practical initial
+    point: it matches the oracle's to the level of its two PCG solves
+    (relative residual 1e-10)."""
+    qp = synth.workload_small() if which == "plain" else synth.workload_box()
+    opt = O.Options(tol=1e-6, ell=20, seed=7)
+    st = O.practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_ipm=0, start_mode=1)
+    box = dict(kind=K8(qp.kind), u=T(qp.u)) if qp.kind is not None else {}
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), None, None, None, **box)
+    got = [x, y, z] + ([info["w"], info["s"]] if box else [])
+    want = [st.x, st.y, st.z] + ([st.w, st.s] if box else [])
+    errs = [relerr(g, v) for g, v in zip(got, want)]
+    print(which, errs)
+    assert max(errs) <= 1e-8
+    assert info["pcg_iters_total"] == 0 and info["ipm_iters"] == 0
+
+
+@pytest.mark.parametrize("which", ["plain", "box"])
+def test_solve_from_practical_start_matches_oracle(nys, which):
+    """A whole solve from the practical start with the oracle's PCG and IPM
+    counts: KKT within tolerance and the iterates agree with the oracle's far
+    below it."""
+    qp = synth.workload_small() if which == "plain" else synth.workload_box()
+    opt = O.Options(tol=1e-6, ell=20, seed=7)
+    ref = O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
+    assert ref.status == "converged"
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=ref.pcg_iters, forced_ipm=ref.ipm_iters,
+                   start_mode=1)
+    box = dict(kind=K8(qp.kind), u=T(qp.u)) if qp.kind is not None else {}
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), None, None, None, **box)
+    assert info["ipm_iters"] == ref.ipm_iters and info["pcg_log"] == ref.pcg_iters
+    for g, v in ((x, ref.x), (y, ref.y), (z, ref.z)):
+        assert relerr(g, v) <= 1e-5
+    assert info["rel_primal"] <= 1e-6 and info["rel_dual"] <= 1e-6 and info["mu"] <= 1e-6
+
+
+def test_practical_start_in_the_precision_form(nys):
+    """start_mode=1 with the precision form (float-float FP32 operator for the
+    two start solves): converges to KKT <= 1e-6 on the FP32 problem."""
+    qp = synth.box_qp(78, 400, 2000, 0.1, 0.3, "exp200")
+    A32 = qp.A.astype(np.float32)
+    A64 = A32.astype(np.float64)
+    b = A64 @ qp.x0
+    c = A64.T @ qp.y0 + qp.z0 - qp.s0 - qp.q * qp.x0
+    h = nys.Handle(qp.m, qp.n, ell=30, tol=1e-6, seed=5, precision_mode=1, start_mode=1)
+    x, y, z, info = nys.nys_solve(h, torch.from_numpy(A32).to(DEV), T(b), T(c), T(qp.q), None, None, None,
+                                  kind=K8(qp.kind), u=T(qp.u))
+    assert info["status"] in (0, 2)
+    rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, *_np(x, y, z), qp.kind, qp.u, *_np(info["w"], info["s"]))
+    assert rp <= 1e-6 and rd <= 1e-6 and mu <= 1e-6
