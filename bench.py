@@ -43,6 +43,14 @@ WORKLOADS = {
     "box-200x500": dict(form="box", m=200, n=500, ell=20, tol=1e-6, gen="box",
                         desc="m=200, n=500, sigma_i=1/i, q~U[0,1], 10% free and 30% box-constrained variables "
                              "(problem (P~)), ell=20, tol 1e-6, FP64 form"),
+    "svm-100x98528": dict(form="box", m=101, n=98628, ell=50, tol=1e-6, gen="svm", start="practical",
+                          desc="dual linear SVM (supplement formulation, (P~): d=100 free, 98528 box variables "
+                               "0<=p<=1), synthetic dense features of the SensIT shape, ell=50, tol 1e-6, "
+                               "practical initial point, FP64 form"),
+    "portfolio-1600x1000x20": dict(form="box", m=1021, n=2620, ell=20, tol=1e-8, gen="portfolio", start="practical",
+                                   desc="factor-model portfolio (supplement formulation, (P~)): 1600 assets, "
+                                        "1000 correlation rows, 20 factors, ell=20, tol 1e-8, practical initial "
+                                        "point, FP64 form"),
     "fp64-5000x20000": dict(form="fp64", m=5000, n=20000, ell=100, tol=1e-8, gen="fp64",
                             desc="m=5000, n=20000, sigma_i=i^-0.8, q 50% zero, ell=100, tol 1e-8, FP64 form"),
     "precision-20000x100000": dict(form="bf16", m=20000, n=100000, ell=400, tol=1e-6, gen="device-exp200",
@@ -156,6 +164,10 @@ def host_workload(w, rank):
         return [synth.workload_small(1235 + off)]
     if g == "box":
         return [synth.workload_box(1240 + off)]
+    if g == "svm":
+        return [synth.svm_qp(1241 + off, 100, 98528)]
+    if g == "portfolio":
+        return [synth.portfolio_qp(1242 + off, 1600, 1000, 20)]
     if g == "fp64":
         return [synth.workload_fp64(1236 + off)]
     if g == "batch":
@@ -255,7 +267,11 @@ def run_reference(args, w, rank, world):
         done = 0
         for qp in probs:
             ell = min(w["ell"], max(1, qp.m // 4)) if w["form"] == "batch" else w["ell"]
-            O.solve_qp(qp, O.Options(tol=w["tol"], ell=ell, seed=seed))
+            opt = O.Options(tol=w["tol"], ell=ell, seed=seed)
+            if args.practical_start:
+                O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
+            else:
+                O.solve_qp(qp, opt)
             done += 1
             if time.perf_counter() - t0 > budget:
                 break
@@ -306,6 +322,8 @@ def main():
         profile_kernel(args)
         return
     w = WORKLOADS[args.workload]
+    if w.get("start") == "practical":
+        args.practical_start = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

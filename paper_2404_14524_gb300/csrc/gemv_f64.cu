@@ -6,9 +6,15 @@
 // band of rows; per-band partial sums go to a split buffer that a second
 // kernel reduces in a fixed order (deterministic, no atomics).
 // A t is a row reduction: one warp per row, 16-byte loads, xor-shuffle sum.
+// When there are too few rows to fill the GPU (short, wide A: m of order 100,
+// n of order 10^5, as in the dual-SVM constraint matrix) each row is also cut
+// into column chunks whose partial sums a second kernel adds in a fixed
+// order (deterministic).
 //
 // On GB300 the FP64 form of these kernels is bound by DFMA throughput (one
 // fused multiply-add per element of A), not by HBM bandwidth.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -83,32 +89,56 @@ __global__ void __launch_bounds__(kNT) k_atv_reduce(int n, int splits, const dou
   t[j] = (D ? D[j] : 1.0) * s;
 }
 
+// Row dot products over columns [c0, c1) (c0 even).  part == nullptr: the
+// whole row, out[row] = sum + beta v[row]; otherwise the chunk's partial sum
+// goes to part[blockIdx.y * m + row].
 template <bool kVec>
 __global__ void __launch_bounds__(kNT) k_av(int m, int n, const double* __restrict__ A, long long lda,
                                             const double* __restrict__ t, double beta,
                                             const double* __restrict__ v, double* __restrict__ out,
-                                            const int* __restrict__ skip, const double* __restrict__ beta_dev) {
+                                            const int* __restrict__ skip, const double* __restrict__ beta_dev,
+                                            int chunk, double* __restrict__ part) {
   if (skip && *skip) return;
-  if (beta_dev) beta = *beta_dev;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (row >= m) return;
+  const int c0 = blockIdx.y * chunk;
+  const int c1 = min(n, c0 + chunk);
   const double* a = A + (long long)row * lda;
   double acc0 = 0.0, acc1 = 0.0;
   if (kVec) {
 #pragma unroll 4
-    for (int j = 2 * lane; j + 1 < n; j += 64) {
+    for (int j = c0 + 2 * lane; j + 1 < c1; j += 64) {
       const double2 x = __ldg(reinterpret_cast<const double2*>(a + j));
       const double2 y = __ldg(reinterpret_cast<const double2*>(t + j));
       acc0 = fma(x.x, y.x, acc0);
       acc1 = fma(x.y, y.y, acc1);
     }
-    if ((n & 1) && lane == 0) acc0 = fma(__ldg(a + n - 1), __ldg(t + n - 1), acc0);
+    if ((c1 & 1) && c1 == n && lane == 0) acc0 = fma(__ldg(a + n - 1), __ldg(t + n - 1), acc0);
   } else {
-    for (int j = lane; j < n; j += 32) acc0 = fma(__ldg(a + j), __ldg(t + j), acc0);
+    for (int j = c0 + lane; j < c1; j += 32) acc0 = fma(__ldg(a + j), __ldg(t + j), acc0);
   }
   double s = warp_sum(acc0 + acc1);
-  if (lane == 0) out[row] = (beta != 0.0) ? fma(beta, v[row], s) : s;
+  if (lane != 0) return;
+  if (part) {
+    part[(size_t)blockIdx.y * m + row] = s;
+    return;
+  }
+  if (beta_dev) beta = *beta_dev;
+  out[row] = (beta != 0.0) ? fma(beta, v[row], s) : s;
+}
+
+// out[row] = sum over the chunks, in chunk order, + beta v[row]
+__global__ void __launch_bounds__(kNT) k_av_reduce(int m, int chunks, const double* __restrict__ part, double beta,
+                                                   const double* __restrict__ v, double* __restrict__ out,
+                                                   const int* __restrict__ skip, const double* __restrict__ beta_dev) {
+  if (skip && *skip) return;
+  const int row = blockIdx.x * kNT + threadIdx.x;
+  if (row >= m) return;
+  if (beta_dev) beta = *beta_dev;
+  double s = 0.0;
+  for (int k = 0; k < chunks; ++k) s += part[(size_t)k * m + row];
+  out[row] = (beta != 0.0) ? fma(beta, v[row], s) : s;
 }
 
 __global__ void k_scaling(int n, const double* __restrict__ x, const double* __restrict__ z,
@@ -155,15 +185,40 @@ cudaError_t gemv_t_f64(cudaStream_t st, int m, int n, const double* A, long long
   return cudaGetLastError();
 }
 
+int av_chunks(int m, int n, size_t split_cap, int* chunk) {
+  // enough (row block, column chunk) pairs for four blocks per SM, chunks of
+  // at least 1024 columns, a multiple of 64 wide (16-byte loads stay aligned)
+  const int blocks = (m + kWarps - 1) / kWarps;
+  long long S = (kTargetBlocks + blocks - 1) / blocks;
+  S = std::min<long long>(S, n / 1024);
+  if (m > 0) S = std::min<long long>(S, (long long)(split_cap / (size_t)m));
+  if (S < 2) {
+    *chunk = n;
+    return 1;
+  }
+  const long long w = ((n + S - 1) / S + 63) / 64 * 64;
+  *chunk = (int)w;
+  return (int)((n + w - 1) / w);
+}
+
 cudaError_t gemv_n_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
                        const double* t, double beta, const double* v, double* out,
-                       const int* skip, const double* beta_dev) {
+                       const int* skip, const double* beta_dev, double* split_buf, size_t split_cap) {
   if (m <= 0) return cudaSuccess;
   const bool vec = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) &&
                    ((reinterpret_cast<uintptr_t>(t) & 15u) == 0);
   const int blocks = (m + kWarps - 1) / kWarps;
-  if (vec) { count_launches(1); k_av<true><<<blocks, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip, beta_dev); }
-  else { count_launches(1); k_av<false><<<blocks, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip, beta_dev); }
+  int chunk = n;
+  const int S = split_buf ? av_chunks(m, n, split_cap, &chunk) : 1;
+  double* part = S > 1 ? split_buf : nullptr;
+  dim3 grid(blocks, S);
+  count_launches(1);
+  if (vec) k_av<true><<<grid, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip, beta_dev, chunk, part);
+  else k_av<false><<<grid, kNT, 0, st>>>(m, n, A, lda, t, beta, v, out, skip, beta_dev, chunk, part);
+  if (S > 1) {
+    count_launches(1);
+    k_av_reduce<<<(m + kNT - 1) / kNT, kNT, 0, st>>>(m, S, split_buf, beta, v, out, skip, beta_dev);
+  }
   return cudaGetLastError();
 }
 

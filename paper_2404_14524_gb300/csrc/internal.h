@@ -54,10 +54,13 @@ cudaError_t gemv_t_f64(cudaStream_t st, int m, int n, const double* A, long long
                        const double* v, const double* D, double* t, double* split_buf,
                        size_t split_cap, const int* skip = nullptr);
 // out[i] = sum_j A[i, j] t[j] + beta * v[i]   (v may be nullptr when beta == 0);
-// when beta_dev is given, beta is read from device memory instead.
+// when beta_dev is given, beta is read from device memory instead.  With a
+// split buffer, rows too few to fill the GPU are cut into column chunks
+// (partials in split_buf, then a fixed-order sum).
 cudaError_t gemv_n_f64(cudaStream_t st, int m, int n, const double* A, long long lda,
                        const double* t, double beta, const double* v, double* out,
-                       const int* skip = nullptr, const double* beta_dev = nullptr);
+                       const int* skip = nullptr, const double* beta_dev = nullptr,
+                       double* split_buf = nullptr, size_t split_cap = 0);
 // Rows of split-reduction scratch that gemv_t_f64 needs for an m x n matrix.
 size_t gemv_t_split_elems(int m, int n);
 

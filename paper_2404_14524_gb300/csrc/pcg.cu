@@ -287,7 +287,7 @@ cudaError_t pcg_iteration_f64(cudaStream_t st, int m, int n, const double* A, lo
   const int* done = si + SI_DONE;
   cudaError_t e = gemv_t_f64(st, m, n, A, lda, w.p, D, w.t, w.split_buf, w.split_cap, done);
   if (e != cudaSuccess) return e;
-  e = gemv_n_f64(st, m, n, A, lda, w.t, 1.0, w.p, w.w, done, sd + SD_DELTA);
+  e = gemv_n_f64(st, m, n, A, lda, w.t, 1.0, w.p, w.w, done, sd + SD_DELTA, w.split_buf, w.split_cap);
   if (e != cudaSuccess) return e;
   return pcg_tail(st, m, ell, U, ld, w, sd, si, red);
 }

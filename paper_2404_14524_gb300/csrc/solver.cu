@@ -527,7 +527,8 @@ int newton_begin(nys_solver* h, int m, int n, const double* A, long long lda, co
                  const BoxTerms* bt = nullptr) {
   const int rc = newton_rhs(h, n, x, D, r_d, r_xz, bt);
   if (rc != NYS_OK) return rc;
-  CK(gemv_n_f64(h->st, m, n, A, lda, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi));
+  CK(gemv_n_f64(h->st, m, n, A, lda, h->t_n, r_p ? 1.0 : 0.0, r_p, h->xi, nullptr, nullptr, h->split_buf,
+                h->split_cap));
   return NYS_OK;
 }
 
@@ -566,7 +567,7 @@ struct Prob {
 // out = A x + beta v (accurate: FP64 A, or FP32 A with float-float sums)
 int op_Ax(nys_solver* h, const Prob& P, const double* x, double beta, const double* v, double* out) {
   if (!P.lp) {
-    CK(gemv_n_f64(h->st, P.m, P.n, P.A64, P.lda, x, beta, v, out));
+    CK(gemv_n_f64(h->st, P.m, P.n, P.A64, P.lda, x, beta, v, out, nullptr, nullptr, h->split_buf, h->split_cap));
   } else {
     CK(split_ff(h->st, P.n, (int)align_up(P.n, 8), x, nullptr, h->fh, h->fl));
     CK(gemv_rows_ff(h->st, P.m, P.n, P.Af, P.lda, h->fh, h->fl, nullptr, beta, v, out, nullptr, nullptr,
@@ -1487,7 +1488,7 @@ int nys_normal_matvec(nys_handle h, int m, int n, int a_dtype, const void* A, lo
     return fail(h, NYS_ERR_ARG, "nys_normal_matvec: bad argument");
   const double* Ad = static_cast<const double*>(A);
   CK(gemv_t_f64(h->st, m, n, Ad, lda, v, D, h->pw.t, h->split_buf, h->split_cap));
-  CK(gemv_n_f64(h->st, m, n, Ad, lda, h->pw.t, delta, v, out));
+  CK(gemv_n_f64(h->st, m, n, Ad, lda, h->pw.t, delta, v, out, nullptr, nullptr, h->split_buf, h->split_cap));
   return NYS_OK;
 }
 
@@ -1772,7 +1773,8 @@ int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result*
                         h->num_sms));
     // (N + delta I) lam2 = A (D .* g)
     CK(vmul_f64(h->st, n, h->D, g, h->t_n));
-    CK(gemv_n_f64(h->st, m, n, A, P.lda, h->t_n, 0.0, nullptr, h->xi));
+    CK(gemv_n_f64(h->st, m, n, A, P.lda, h->t_n, 0.0, nullptr, h->xi, nullptr, nullptr, h->split_buf,
+                  h->split_cap));
     int it = 0;
     int rc = run_pcg(h, m, n, A, P.lda, h->D, R.delta, ell, h->U, h->ld, h->lamh, h->xi, h->dyp, eta,
                      h->opt.max_pcg_iter, -1, &it);

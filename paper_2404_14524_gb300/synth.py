@@ -123,6 +123,80 @@ def box_qp(seed: int, m: int, n: int, frac_free: float = 0.1, frac_box: float = 
                            name=f"box-{sigma_kind}-{m}x{n}-f{frac_free}-b{frac_box}-s{seed}")
 
 
+def svm_qp(seed: int, d: int, n_samples: int, tau: float = 1.0, sep: float = 1.0) -> QP:
+    """Dual linear SVM with l1 slack penalty, written as (P~) (the supplement's
+    SVM formulation): x = (v, p), v in R^d free, 0 <= p_i <= tau;
+    A = [[I_d, -X diag(lab)], [0, lab^T]], b = 0, Q = diag(1_d, 0_n),
+    c = (0_d, -1_n) (the objective 1/2 v^T v - sum p_i).
+    Synthetic dense features stand in for the SVM datasets: balanced labels
+    lab = +-1, samples X_i = (lab_i * mu + g_i) / sqrt(d) with mu ~ sep * N(0, I_d)
+    and g_i ~ N(0, I_d) (every entry non-zero).  Start (interior; primal
+    feasible when n_samples is even): p0 = tau/2, v0 = X diag(lab) p0,
+    y0 = 0, z0 = s0 = 1 on J."""
+    rng = np.random.default_rng(seed)
+    lab = np.where(rng.permutation(n_samples) < n_samples // 2, 1.0, -1.0)
+    mu = sep * rng.standard_normal(d)
+    X = (lab[None, :] * mu[:, None] + rng.standard_normal((d, n_samples))) / np.sqrt(d)
+    m, n = d + 1, d + n_samples
+    A = np.zeros((m, n))
+    A[:d, :d] = np.eye(d)
+    A[:d, d:] = -X * lab[None, :]
+    A[d, d:] = lab
+    q = np.concatenate([np.ones(d), np.zeros(n_samples)])
+    c = np.concatenate([np.zeros(d), -np.ones(n_samples)])
+    kind = np.concatenate([np.full(d, KIND_F), np.full(n_samples, KIND_J)]).astype(np.int8)
+    u = np.concatenate([np.zeros(d), np.full(n_samples, tau)])
+    p0 = np.full(n_samples, 0.5 * tau)
+    x0 = np.concatenate([(X * lab[None, :]) @ p0, p0])
+    z0 = np.concatenate([np.zeros(d), np.ones(n_samples)])
+    s0 = np.concatenate([np.zeros(d), np.ones(n_samples)])
+    return QP(A=np.ascontiguousarray(A), b=np.zeros(m), c=c, q=q, x0=x0, y0=np.zeros(m), z0=z0,
+              name=f"svm-{d}x{n_samples}-s{seed}", kind=kind, u=u, s0=s0)
+
+
+def portfolio_qp(seed: int, n_assets: int, d: int, s: int, gamma: float = 1.0) -> QP:
+    """Factor-model portfolio problem of the supplement, written as (P~):
+    minimise -r^T x / gamma + x^T Dg x + y^T y subject to y = F^T x, M x <= u,
+    1^T x = 1, x >= 0, y free.  Variables (x, y, t) with the slack t >= 0 of
+    M x + t = u: A = [[F^T, -I_s, 0], [M, 0, I_d], [1^T, 0, 0]],
+    b = (0_s, u, 1), Q = diag(2 Dg, 2 1_s, 0_d), c = (-r / gamma, 0, 0).
+    Risk model: Sigma = U diag(lam) U^T + 0.01 I with U Haar (n x 2s) and a
+    spectrum that decays fast over the first s and slowly after
+    (lam_i = exp(-8 i / s) for i <= s, then 0.01 (s / i)^0.5); F = the top-s
+    eigenpairs U_s diag(lam_s)^{1/2} and Dg = diag(Sigma - F F^T) (exact
+    eigenpairs stand in for the paper's randomized Nystrom risk model).
+    M rows ~ N(0, I_n); r ~ N(0, 1); u ~ U[0, 1], raised where needed to
+    M 1/n + 1e-3 so that the equal-weight portfolio is feasible.  Start
+    (interior): x0 = 1/n, y0' = F^T x0, t0 = u - M x0; dual y0 = 0, z0 = 1
+    on x and t, 0 on the free y."""
+    rng = np.random.default_rng(seed)
+    k = 2 * s
+    U = haar_columns(rng, n_assets, k)
+    i = np.arange(1, k + 1, dtype=np.float64)
+    lam = np.where(i <= s, np.exp(-8.0 * i / s), 0.01 * np.sqrt(s / i))
+    F = U[:, :s] * np.sqrt(lam[:s])[None, :]
+    Dg = (U[:, s:] ** 2) @ lam[s:] + 0.01
+    M = rng.standard_normal((d, n_assets))
+    r = rng.standard_normal(n_assets)
+    xe = np.full(n_assets, 1.0 / n_assets)
+    u = np.maximum(rng.uniform(0.0, 1.0, d), M @ xe + 1e-3)
+    m, n = s + d + 1, n_assets + s + d
+    A = np.zeros((m, n))
+    A[:s, :n_assets] = F.T
+    A[:s, n_assets:n_assets + s] = -np.eye(s)
+    A[s:s + d, :n_assets] = M
+    A[s:s + d, n_assets + s:] = np.eye(d)
+    A[s + d, :n_assets] = 1.0
+    b = np.concatenate([np.zeros(s), u, [1.0]])
+    q = np.concatenate([2.0 * Dg, np.full(s, 2.0), np.zeros(d)])
+    c = np.concatenate([-r / gamma, np.zeros(s + d)])
+    kind = np.concatenate([np.full(n_assets, KIND_I), np.full(s, KIND_F), np.full(d, KIND_I)]).astype(np.int8)
+    x0 = np.concatenate([xe, F.T @ xe, u - M @ xe])
+    z0 = np.concatenate([np.ones(n_assets), np.zeros(s), np.ones(d)])
+    return QP(A=np.ascontiguousarray(A), b=b, c=c, q=q, x0=x0, y0=np.zeros(m), z0=z0,
+              name=f"portfolio-{n_assets}x{d}x{s}-s{seed}", kind=kind, u=np.zeros(n), s0=np.zeros(n))
+
+
 def spectral_qp(seed: int, m: int, n: int, sigma_kind: str, q_kind: str = "uniform") -> QP:
     """Single dense QP with a prescribed spectrum.
 

@@ -336,3 +336,31 @@ def test_practical_start_in_the_precision_form(nys):
     assert info["status"] in (0, 2)
     rp, rd, mu = O.kkt_measures(A64, b, c, qp.q, *_np(x, y, z), qp.kind, qp.u, *_np(info["w"], info["s"]))
     assert rp <= 1e-6 and rd <= 1e-6 and mu <= 1e-6
+
+
+# ------------------------------------------------ SVM- and portfolio-shaped problems
+
+@pytest.mark.parametrize("which", ["svm", "portfolio"])
+def test_svm_and_portfolio_problems_match_oracle(nys, which):
+    """The supplement's two (P~) formulations on small synthetic instances
+    (dual SVM: free v, box-constrained p; factor-model portfolio: free factor
+    exposures, non-negative weights and slacks), solved from the practical
+    start with the oracle's PCG and IPM counts: iterates agree to 1e-6 (the
+    oracle's own response to a 2e-16 change of Omega is 1e-11 / 3e-10 here)
+    and the KKT measures meet the tolerance."""
+    if which == "svm":
+        qp, tol, ell = synth.svm_qp(5, 20, 800), 1e-6, 10
+    else:
+        qp, tol, ell = synth.portfolio_qp(6, 400, 250, 10), 1e-8, 20
+    opt = O.Options(tol=tol, ell=ell, seed=3)
+    ref = O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
+    assert ref.status == "converged"
+    h = nys.Handle(qp.m, qp.n, ell=ell, tol=tol, seed=3, forced_pcg=ref.pcg_iters, forced_ipm=ref.ipm_iters,
+                   start_mode=1)
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), None, None, None, kind=K8(qp.kind),
+                                  u=T(qp.u))
+    assert info["ipm_iters"] == ref.ipm_iters and info["pcg_log"] == ref.pcg_iters
+    for g, v in ((x, ref.x), (y, ref.y), (z, ref.z), (info["w"], ref.w), (info["s"], ref.s)):
+        assert relerr(g, v) <= 1e-6
+    rp, rd, mu = O.kkt_measures(qp.A, qp.b, qp.c, qp.q, *_np(x, y, z), qp.kind, qp.u, *_np(info["w"], info["s"]))
+    assert rp <= tol and rd <= tol and mu <= tol

@@ -58,7 +58,7 @@ def test_gaussian_matches_oracle(nys, m, ell, k):
 
 # -------------------------------------------------------------- a1, a2
 
-@pytest.mark.parametrize("m,n", [(203, 517), (1, 1), (64, 1025), (777, 129)])
+@pytest.mark.parametrize("m,n", [(203, 517), (1, 1), (64, 1025), (777, 129), (101, 98628), (37, 70001), (9, 4097)])
 def test_scaling_and_normal_matvec(nys, m, n):
     rng = np.random.default_rng(m * 7 + n)
     A = rng.standard_normal((m, n))

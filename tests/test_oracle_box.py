@@ -409,3 +409,58 @@ def test_solve_from_practical_start_reaches_the_same_solution():
         b = O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
         assert a.status == "converged" and b.status == "converged" and b.ipm_iters < 60
         assert np.linalg.norm(a.x - b.x) <= 1e-5 * np.linalg.norm(a.x)
+
+
+# ------------------------------------------ SVM- and portfolio-shaped problems
+
+def test_svm_formulation_matches_a_library_svm():
+    """The supplement's dual-SVM (P~) (free v, 0 <= p <= tau, A = [[I, -X diag(lab)],
+    [0, lab^T]]) solved by the oracle from the practical start gives the
+    separating hyperplane of scikit-learn's linear C-SVM (libsvm) with
+    C = tau; the (P~) multipliers reproduce the SVM margin conditions
+    (lab_i (x_i^T v + b0) >= 1 where p_i = 0, = 1 inside the box, <= 1 at tau)."""
+    svm = pytest.importorskip("sklearn.svm")
+    d, ns, tau = 6, 120, 1.0
+    qp = synth.svm_qp(11, d, ns, tau=tau, sep=0.8)
+    r = O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, O.Options(tol=1e-10, ell=d + 1, seed=1),
+                                     qp.kind, qp.u)
+    assert r.status == "converged"
+    v, p = r.x[:d], r.x[d:]
+    Xs = -qp.A[:d, d:] * qp.A[d, d:][None, :]          # recover X from -X diag(lab) and lab^T
+    lab = qp.A[d, d:]
+    ref = svm.SVC(kernel="linear", C=tau, tol=1e-12).fit(Xs.T, lab)
+    assert np.allclose(v, ref.coef_[0], atol=1e-5)
+    b0 = -r.y[d]
+    margin = lab * (Xs.T @ v + b0)
+    assert abs(b0 - ref.intercept_[0]) < 1e-4
+    assert np.all(margin[p < 1e-8] >= 1 - 1e-6)
+    inside = (p > 1e-6) & (p < tau - 1e-6)
+    assert np.allclose(margin[inside], 1.0, atol=1e-5)
+    assert np.all(margin[p > tau - 1e-8] <= 1 + 1e-6)
+
+
+def test_portfolio_formulation_matches_the_original_problem():
+    """The factor-model (P~) (variables x, y = F^T x, slack t) reaches the same
+    optimum as scipy's SLSQP on the original problem
+    min -r^T x / gamma + x^T (F F^T + Dg) x s.t. M x <= u, 1^T x = 1, x >= 0."""
+    na, dd, s = 12, 5, 3
+    qp = synth.portfolio_qp(13, na, dd, s)
+    r = O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, O.Options(tol=1e-10, ell=dd + s + 1, seed=2),
+                                     qp.kind, qp.u)
+    assert r.status == "converged"
+    F = qp.A[:s, :na].T
+    M = qp.A[s:s + dd, :na]
+    u = qp.b[s:s + dd]
+    Dg = 0.5 * qp.q[:na]
+    rr = -qp.c[:na]
+    Sig = F @ F.T + np.diag(Dg)
+    f = lambda x: -rr @ x + x @ Sig @ x
+    cons = [{"type": "ineq", "fun": lambda x: u - M @ x, "jac": lambda x: -M},
+            {"type": "eq", "fun": lambda x: np.sum(x) - 1.0, "jac": lambda x: np.ones((1, na))}]
+    ref = scipy.optimize.minimize(f, np.full(na, 1.0 / na), jac=lambda x: -rr + 2 * Sig @ x, method="SLSQP",
+                                  bounds=[(0, None)] * na, constraints=cons, options={"ftol": 1e-14, "maxiter": 500})
+    assert ref.success
+    x = r.x[:na]
+    assert abs(f(x) - ref.fun) <= 1e-7 * (1 + abs(ref.fun))
+    assert np.allclose(x, ref.x, atol=1e-5)
+    assert np.allclose(r.x[na:na + s], F.T @ x, atol=1e-8)          # y = F^T x
