@@ -217,7 +217,7 @@ def oracle_component_times(A64, b, c, q, x0, y0, z0, ell, tol, seed, box=None):
     return t_ipm, (time.perf_counter() - t0) / k
 
 
-def cpu_baseline(problems, w, runs, seed, practical=False):
+def cpu_baseline(problems, w, runs, seed, practical=False, reuse=0):
     """The oracle as it stands on this host's cores: a whole solve when one
     takes at most ~30 s (else timed components extrapolated with the GPU
     run's iteration counts)."""
@@ -233,7 +233,7 @@ def cpu_baseline(problems, w, runs, seed, practical=False):
     if est * per_step <= 30.0:
         t0 = time.perf_counter()
         for p in problems:
-            opt = O.Options(tol=w["tol"], ell=p["ell"], seed=seed)
+            opt = O.Options(tol=w["tol"], ell=p["ell"], seed=seed, reuse_pcg=reuse)
             if practical:
                 bx = p.get("box") or {}
                 O.solve_from_practical_start(p["A64"], p["b"], p["c"], p["q"], opt, bx.get("kind"), bx.get("u"))
@@ -267,7 +267,7 @@ def run_reference(args, w, rank, world):
         done = 0
         for qp in probs:
             ell = min(w["ell"], max(1, qp.m // 4)) if w["form"] == "batch" else w["ell"]
-            opt = O.Options(tol=w["tol"], ell=ell, seed=seed)
+            opt = O.Options(tol=w["tol"], ell=ell, seed=seed, reuse_pcg=args.reuse_pcg)
             if args.practical_start:
                 O.solve_from_practical_start(qp.A, qp.b, qp.c, qp.q, opt, qp.kind, qp.u)
             else:
@@ -309,6 +309,9 @@ def main():
     ap.add_argument("--practical-start", action="store_true",
                     help="start every solve at the practical initial point (start_mode=1) instead of the "
                          "workload's interior point")
+    ap.add_argument("--reuse-pcg", type=int, default=0,
+                    help="keep the Nystrom factor while both PCG solves of an IPM iteration take at most this "
+                         "many iterations (0: a fresh sketch every iteration, Algorithm 6 as written)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision workloads: also time one FP64-form solve of the same QP")
     ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm", "ff_pcg", "bf16_pcg"],
@@ -365,11 +368,12 @@ def main():
 
     with torch.cuda.stream(stream):
         if form == "batch":
-            h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=32, stream=stream)
+            h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=32, stream=stream,
+                           reuse_pcg=args.reuse_pcg)
         else:
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream,
                            precision_mode={"bf16": 1, "fp8": 2}.get(form, 0),
-                           start_mode=1 if args.practical_start else 0)
+                           start_mode=1 if args.practical_start else 0, reuse_pcg=args.reuse_pcg)
         # the start point the solves receive (None: the practical start computes it)
         start = (lambda pr: pr[4:7]) if not args.practical_start else (lambda pr: (None, None, None))
 
@@ -521,7 +525,7 @@ def main():
                 probs.append(dict(A64=pr[0].double().cpu().numpy(), b=pr[1].cpu().numpy(), c=pr[2].cpu().numpy(),
                                   q=pr[3].cpu().numpy(), x0=pr[4].cpu().numpy(), y0=pr[5].cpu().numpy(),
                                   z0=pr[6].cpu().numpy(), ell=pr[7]))
-            cpu = cpu_baseline(probs, w, runs, seed, args.practical_start)
+            cpu = cpu_baseline(probs, w, runs, seed, args.practical_start, args.reuse_pcg)
         line = {
             "metric": "QP solves/s to KKT tol", "value": value, "unit": "QP solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -531,11 +535,13 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
                        "start": "practical initial point" if args.practical_start else "workload interior point",
+                       "reuse_pcg": args.reuse_pcg,
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6
                        else f"A = {a_bytes / 1e6:.1f} MB fits in L2 (no flush; latency-bound)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "solve": {"status": max(r["status"] for r in runs), "ipm_iters": last["ipm_iters"],
+                      "sketches": last.get("sketches"),
                       "pcg_iters": last["pcg_iters_total"], "refine_steps": last["refine_steps"],
                       "rel_primal": max(r["rel_primal"] for r in runs), "rel_dual": max(r["rel_dual"] for r in runs),
                       "mu": max(r["mu"] for r in runs)},

@@ -79,6 +79,13 @@ typedef struct {
      * the printed x~ + delta_d is read as the primal shift).  With 1 the
      * problem's x0, y0, z0, w0, s0 are ignored and may be NULL. */
     int start_mode;
+    /* Preconditioner reuse (the paper suggests reusing the preconditioner
+     * between IPM iterations without giving a rule): 0 = a fresh sketch and
+     * Nystrom factor in every IPM iteration (Algorithm 6 as written); R > 0 =
+     * keep the previous iteration's factor (U, Lambda; P^{-1} is rebuilt with
+     * the current delta) while both PCG solves of the previous iteration took
+     * at most R iterations. */
+    int reuse_pcg;
 } nys_options;
 
 /* One QP.  With host == 0 all pointers are device pointers; with host == 1
@@ -146,6 +153,7 @@ typedef struct {
     int pcg_log_len;              /* entries written                                   */
     double *w, *s;                /* n each, NULL = not wanted: final slack and bound */
                                   /*   multiplier of a (P~) problem (0 outside J)     */
+    int sketches;                 /* Nystrom factors built (= ipm_iters unless reused) */
 } nys_result;
 
 /* Fill *opt with the defaults listed above. */

@@ -384,6 +384,7 @@ class Options:
     reg_floor: float = 5e-10     # floor seen in Tables 7-8
     forced_pcg: list | None = None   # per Newton solve: predictor, corrector, ...
     forced_ipm: int | None = None
+    reuse_pcg: int = 0           # > 0: keep the Nystrom factor while PCG stays at or under this many iterations
 
 
 @dataclasses.dataclass
@@ -402,6 +403,7 @@ class IterRecord:
     pcg_pred: int
     pcg_corr: int
     state: tuple | None = None
+    reused: bool = False         # the Nystrom factor of the previous iteration was kept
 
 
 @dataclasses.dataclass
@@ -519,8 +521,15 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         x_top, y_top, z_top = x.copy(), y.copy(), z.copy()
         w_top, s_top = (w.copy(), s.copy()) if box else (None, None)
         D = scaling_D(x, z, q, rho, kind, w, s)
-        Omega = gaussian_omega(opt.seed, k0 + k, m, ell)
-        F = nystrom(A, D, Omega)
+        # READING (preconditioner reuse, which the paper only suggests): with
+        # opt.reuse_pcg = R > 0 the factor of the previous iteration is kept
+        # when both of its PCG solves took at most R iterations; otherwise (and
+        # always with R = 0, Algorithm 6 as written) N_k is sketched afresh.
+        reuse = (opt.reuse_pcg > 0 and k > 0 and pcg_counts[-2] <= opt.reuse_pcg
+                 and pcg_counts[-1] <= opt.reuse_pcg)
+        if not reuse:
+            Omega = gaussian_omega(opt.seed, k0 + k, m, ell)
+            F = nystrom(A, D, Omega)
         eta = pcg_tolerance(mu)
         # Predictor (Algorithm 5, first step; Eq. predictor-RHS).
         Ax, Aty = A @ x, A.T @ y
@@ -571,7 +580,7 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         rec = IterRecord(k=k0 + k, mu=mu, rel_p=rel_p, rel_d=rel_d, rho=rho, delta=delta, nu=F.nu,
                          lam_max=float(F.lam[0]), lam_min=float(F.lam[-1]),
                          alpha_p=alpha_p, alpha_d=alpha_d,
-                         pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters)
+                         pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters, reused=reuse)
         if record:
             rec.state = (x_top, y_top, z_top, state_lam, state_zeta)
             if box:

@@ -749,6 +749,8 @@ struct IpmRun {
   double n_mu = 0.0;            // |I u J| + |J|, the divisor of mu
   double pnorm = 0.0;           // ||(b, u_J)||, the scale of the primal residual
   int forced_idx = 0, warn = NYS_OK, k = 0, status = NYS_WARN_MAXITER;
+  int last_pred = 0, last_corr = 0;   // PCG counts of the previous iteration (preconditioner reuse)
+  bool reused = false;                // this iteration kept the previous Nystrom factor
   int pcg_before = 0, ref_before = 0;
   bool done = false;
   PcgRequest req;
@@ -830,6 +832,7 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   r->refine_steps = 0;
   r->pcg_log_len = 0;
   r->pcg_seconds = 0.0;
+  r->sketches = 0;
   h->pcg_ms = 0.0;
   done = true;                 // until the setup below succeeds
   status = NYS_ERR_CUDA;
@@ -1062,14 +1065,20 @@ int IpmRun::top() {
   }
   if (k >= o.max_ipm_iter) { stop(NYS_WARN_MAXITER); return NYS_OK; }
 
-  // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).
+  // N_k, Omega_k, Nystrom preconditioner (Algorithms 1-2).  With reuse_pcg
+  // = R > 0 the previous factor is kept while the previous iteration's two
+  // PCG solves took at most R iterations each.
   tk0 = std::chrono::steady_clock::now();
   if (box) CK(box_scaling_f64(h->st, n, h->vk, h->x, h->z, h->w, h->s, q, rho, h->D));
   else CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
-  rc = op_sketch(h, P, p->k0 + k, ell, h->D);
-  if (rc != NYS_OK) { stop(rc); return rc; }
-  CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
-                      h->cw, h->num_sms));
+  reused = o.reuse_pcg > 0 && k > 0 && last_pred <= o.reuse_pcg && last_corr <= o.reuse_pcg;
+  if (!reused) {
+    rc = op_sketch(h, P, p->k0 + k, ell, h->D);
+    if (rc != NYS_OK) { stop(rc); return rc; }
+    CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
+                        h->cw, h->num_sms));
+    ++r->sketches;
+  }
   eta = std::max(1e-10, std::min(1e-2, 0.1 * mu));
   t_pre = 0.0;
   if (h->trace) {
@@ -1102,6 +1111,7 @@ int IpmRun::top() {
 // corrector's Newton system.
 int IpmRun::mid() {
   const nys_options& o = h->opt;
+  last_pred = req.iters;
   if (!take_request()) return status;
   const BoxTerms btp_ = terms(false), btc_ = terms(true);
   const BoxTerms* btp = box ? &btp_ : nullptr;
@@ -1147,6 +1157,7 @@ int IpmRun::mid() {
 
 // After the corrector's PCG: the combined direction and the step.
 int IpmRun::bottom() {
+  last_corr = req.iters;
   if (!take_request()) return status;
   const BoxTerms btc_ = terms(true);
   if (!lp) {
@@ -1175,9 +1186,10 @@ int IpmRun::bottom() {
     const double t_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - tk0).count();
     std::fprintf(stderr,
                  "[nys] k=%d mu=%.3e rel_p=%.3e rel_d=%.3e rho=%.2e delta=%.2e ap=%.3f ad=%.3f pcg=%d "
-                 "refine=%d sketch+core=%.1fms jacobi_sweeps=%d iter=%.1fms\n",
+                 "refine=%d sketch+core=%.1fms%s jacobi_sweeps=%d iter=%.1fms\n",
                  k, mu, rel_p, rel_d, rho, delta, ap, ad, r->pcg_iters_total - pcg_before,
-                 r->refine_steps - ref_before, 1e3 * t_pre, h->h_si[SI_SWEEPS], 1e3 * t_it);
+                 r->refine_steps - ref_before, 1e3 * t_pre, reused ? " (reused)" : "", h->h_si[SI_SWEEPS],
+                 1e3 * t_it);
   }
   mu_prev = mu;
   ++k;
@@ -1370,6 +1382,7 @@ void nys_default_options(nys_options* o) {
   o->n_forced_pcg = 0;
   o->forced_ipm_iters = -1;
   o->start_mode = 0;
+  o->reuse_pcg = 0;
 }
 
 const char* nys_last_error(nys_handle h) { return h ? h->err.c_str() : "null handle"; }

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("precision_mode", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("reg_floor", ctypes.c_double),
                 ("forced_pcg_iters", ctypes.POINTER(ctypes.c_int)), ("n_forced_pcg", ctypes.c_int),
-                ("forced_ipm_iters", ctypes.c_int), ("start_mode", ctypes.c_int)]
+                ("forced_ipm_iters", ctypes.c_int), ("start_mode", ctypes.c_int), ("reuse_pcg", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -72,7 +72,8 @@ class Result(ctypes.Structure):
                 ("mu", ctypes.c_double), ("rel_gap", ctypes.c_double), ("rho", ctypes.c_double),
                 ("delta", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("pcg_seconds", ctypes.c_double), ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
-                ("pcg_log_len", ctypes.c_int), ("w", ctypes.c_void_p), ("s", ctypes.c_void_p)]
+                ("pcg_log_len", ctypes.c_int), ("w", ctypes.c_void_p), ("s", ctypes.c_void_p),
+                ("sketches", ctypes.c_int)]
 
 
 _lib = None
@@ -465,7 +466,7 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
         h.check(rc)
     info = {k: getattr(r, k) for k in ("status", "ipm_iters", "pcg_iters_total", "refine_steps",
                                        "rel_primal", "rel_dual", "mu", "rel_gap", "rho", "delta",
-                                       "seconds", "pcg_seconds")}
+                                       "seconds", "pcg_seconds", "sketches")}
     info["pcg_log"] = list(log[: r.pcg_log_len])
     if want_pmm:
         info["lam"], info["zeta"] = lam, zeta
@@ -554,7 +555,7 @@ def nys_solve_batched(h: Handle, problems, check: bool = True):
     for i, (x, y, z, w, s) in enumerate(outs):
         info = {f: getattr(R[i], f) for f in ("status", "ipm_iters", "pcg_iters_total", "refine_steps", "rel_primal",
                                               "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds",
-                                              "pcg_seconds")}
+                                              "pcg_seconds", "sketches")}
         if w is not None:
             info["w"], info["s"] = w, s
         res.append((x, y, z, info))

@@ -364,3 +364,27 @@ def test_svm_and_portfolio_problems_match_oracle(nys, which):
         assert relerr(g, v) <= 1e-6
     rp, rd, mu = O.kkt_measures(qp.A, qp.b, qp.c, qp.q, *_np(x, y, z), qp.kind, qp.u, *_np(info["w"], info["s"]))
     assert rp <= tol and rd <= tol and mu <= tol
+
+
+# ------------------------------------------------------- preconditioner reuse
+
+@pytest.mark.parametrize("which", ["plain", "box"])
+def test_preconditioner_reuse_matches_oracle(nys, which):
+    """reuse_pcg = 40: the GPU keeps the factor in the same iterations as the
+    oracle (its decisions follow the PCG counts, here forced to the oracle's)
+    and reaches the same iterates."""
+    qp = synth.workload_small() if which == "plain" else synth.workload_box()
+    opt = O.Options(tol=1e-6, ell=20, seed=7, reuse_pcg=40)
+    ref = O.solve_qp(qp, opt)
+    n_sketch = sum(1 for t in ref.trace if not t.reused)
+    assert n_sketch < ref.ipm_iters
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=ref.pcg_iters, forced_ipm=ref.ipm_iters,
+                   reuse_pcg=40)
+    if which == "plain":
+        x, y, z, info = nys.nys_solve(h, *(T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0)))
+    else:
+        x, y, z, info = _solve(nys, h, qp)
+    assert info["sketches"] == n_sketch and info["pcg_log"] == ref.pcg_iters
+    for g, v in ((x, ref.x), (y, ref.y), (z, ref.z)):
+        assert relerr(g, v) <= 1e-5
+    assert info["rel_primal"] <= 1e-6 and info["rel_dual"] <= 1e-6 and info["mu"] <= 1e-6

@@ -464,3 +464,24 @@ def test_portfolio_formulation_matches_the_original_problem():
     assert abs(f(x) - ref.fun) <= 1e-7 * (1 + abs(ref.fun))
     assert np.allclose(x, ref.x, atol=1e-5)
     assert np.allclose(r.x[na:na + s], F.T @ x, atol=1e-8)          # y = F^T x
+
+
+# ------------------------------------------------------- preconditioner reuse
+
+def test_preconditioner_reuse_reaches_the_same_optimum():
+    """Keeping the previous Nystrom factor while PCG stays cheap (reuse_pcg = R)
+    changes only the preconditioner, never the Newton systems: the solve
+    still meets the KKT tolerance at the same optimum, with fewer sketches;
+    R = 0 is Algorithm 6 as written (a factor in every iteration)."""
+    qp = synth.workload_small()
+    base = O.solve_qp(qp, O.Options(tol=1e-8, ell=20, seed=7))
+    assert all(not t.reused for t in base.trace)
+    r = O.solve_qp(qp, O.Options(tol=1e-8, ell=20, seed=7, reuse_pcg=60))
+    assert r.status == "converged"
+    reused = [t.reused for t in r.trace]
+    assert 0 < sum(reused) < len(reused) and not reused[0]
+    # the rule: a factor is kept exactly when both previous solves took <= R iterations
+    for k in range(1, len(r.trace)):
+        prev = r.trace[k - 1]
+        assert reused[k] == (prev.pcg_pred <= 60 and prev.pcg_corr <= 60)
+    assert np.linalg.norm(r.x - base.x) <= 1e-6 * np.linalg.norm(base.x)
