@@ -439,8 +439,12 @@ def main():
             fl = sum(pcg_flops_per_iter(pr[0].shape[0], pr[0].shape[1], pr[7]) * i["pcg_iters_total"]
                      for pr, i in zip(dev_probs * args.steps, timed))
             peak = fp64_alu_peak_tflops()
+            # DRAM bytes of one launch from the committed ncu capture of this
+            # workload's cluster kernel (None when the kernel changed since)
+            tr = traffic_record("pcg_cluster.cu", "pcg_cluster_small-fp64") \
+                if args.workload == "small-fp64" and routes == ["cluster-smem"] else None
             roofline = {"bound": "alu", "achieved": fl / pcg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "frac": fl / pcg_s / 1e12 / peak, "traffic": None,
+                        "frac": fl / pcg_s / 1e12 / peak, "traffic": tr["bytes_per_launch"] if tr else None,
                         "kernel": "whole-PCG kernel (" + ", ".join(routes) + "), one launch per Newton solve",
                         "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
                         "launch_avg_ms": 1e3 * pcg_s / max(1, 2 * sum(i["ipm_iters"] for i in timed)),
