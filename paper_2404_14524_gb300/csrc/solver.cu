@@ -121,6 +121,10 @@ struct nys_solver {
   int max_batch = 0;
   std::vector<nys_solver*> workers;
   std::vector<cudaStream_t> worker_streams;
+  // shared launches of one Newton phase: one stream per launch shape, so that
+  // groups of different cluster size run side by side
+  std::vector<cudaStream_t> group_streams;
+  std::vector<cudaEvent_t> group_events;
 };
 
 namespace {
@@ -1306,6 +1310,7 @@ int serve_batch(nys_solver* master, std::vector<IpmRun>& runs, std::vector<Batch
   }
   CK(cudaEventRecord(master->ev_b0, master->st));
   size_t g0 = 0;
+  int gi = 0;
   while (g0 < idx.size()) {
     size_t g1 = g0;
     ClusterPlan gp = slots[idx[g0]].plan;
@@ -1324,9 +1329,27 @@ int serve_batch(nys_solver* master, std::vector<IpmRun>& runs, std::vector<Batch
       t.delta = q.delta; t.eta2 = q.eta * q.eta; t.max_iter = q.max_iter; t.forced = q.forced;
       t.x = q.out; t.iters = w->si + SI_ITERS; t.sd = w->sd; t.err = w->si + SI_ERR;
     }
+    // each launch shape on a stream of its own, forked from and joined back
+    // into the master stream (groups run concurrently, not one after another)
+    if (gi >= (int)master->group_streams.size()) {
+      cudaStream_t gs = nullptr;
+      cudaEvent_t ge = nullptr;
+      CK(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+      if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(gs);
+        return fail(h, NYS_ERR_CUDA, "serve_batch: cannot create a group event");
+      }
+      master->group_streams.push_back(gs);
+      master->group_events.push_back(ge);
+    }
+    cudaStream_t gs = master->group_streams[gi];
+    CK(cudaStreamWaitEvent(gs, master->ev_b0, 0));
     CK(cudaMemcpyAsync(master->d_tasks + g0, master->h_tasks + g0, sizeof(ClusterPcgTask) * (g1 - g0),
-                       cudaMemcpyHostToDevice, master->st));
-    CK(pcg_cluster_f64(master->st, gp, master->h_tasks[g0], master->d_tasks + g0, (int)(g1 - g0)));
+                       cudaMemcpyHostToDevice, gs));
+    CK(pcg_cluster_f64(gs, gp, master->h_tasks[g0], master->d_tasks + g0, (int)(g1 - g0)));
+    CK(cudaEventRecord(master->group_events[gi], gs));
+    CK(cudaStreamWaitEvent(master->st, master->group_events[gi], 0));
+    ++gi;
     g0 = g1;
   }
   CK(cudaEventRecord(master->ev_b1, master->st));
@@ -1464,6 +1487,8 @@ int nys_destroy(nys_handle h) {
   if (!h) return NYS_ERR_ARG;
   for (nys_solver* w : h->workers) nys_destroy(w);
   for (cudaStream_t s : h->worker_streams) cudaStreamDestroy(s);
+  for (cudaStream_t s : h->group_streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : h->group_events) cudaEventDestroy(e);
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   drop_pcg_graph(h);
