@@ -309,6 +309,9 @@ def main():
     ap.add_argument("--practical-start", action="store_true",
                     help="start every solve at the practical initial point (start_mode=1) instead of the "
                          "workload's interior point")
+    ap.add_argument("--max-batch", type=int, default=None,
+                    help="batch workloads: solves in flight at once (worker solvers of nys_solve_batched; "
+                         "default: the whole batch)")
     ap.add_argument("--reuse-pcg", type=int, default=0,
                     help="keep the Nystrom factor while both PCG solves of an IPM iteration take at most this "
                          "many iterations (0: a fresh sketch every iteration, Algorithm 6 as written)")
@@ -325,6 +328,8 @@ def main():
         profile_kernel(args)
         return
     w = WORKLOADS[args.workload]
+    if args.max_batch is None:
+        args.max_batch = w.get("count", 32)
     if w.get("start") == "practical":
         args.practical_start = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -368,8 +373,8 @@ def main():
 
     with torch.cuda.stream(stream):
         if form == "batch":
-            h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=32, stream=stream,
-                           reuse_pcg=args.reuse_pcg)
+            h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=args.max_batch,
+                           stream=stream, reuse_pcg=args.reuse_pcg)
         else:
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream,
                            precision_mode={"bf16": 1, "fp8": 2}.get(form, 0),
@@ -539,6 +544,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
                        "start": "practical initial point" if args.practical_start else "workload interior point",
+                       "max_batch": args.max_batch if form == "batch" else None,
                        "reuse_pcg": args.reuse_pcg,
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6
