@@ -372,7 +372,7 @@ def main():
     a_bytes = sum(p[0].numel() * p[0].element_size() for p in dev_probs)
 
     with torch.cuda.stream(stream):
-        if form == "batch":
+        if form in ("batch", "diff"):
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, max_batch=args.max_batch,
                            stream=stream, reuse_pcg=args.reuse_pcg)
         else:
@@ -385,6 +385,15 @@ def main():
         def step():
             if form == "batch":
                 return [r[3] for r in nys.nys_solve_batched(h, dev_probs)]
+            if form == "diff":
+                # forward solves of the whole batch in one call, then the adjoints
+                out = []
+                for k, (x, y, z, info) in enumerate(nys.nys_solve_batched(h, dev_probs)):
+                    pr = dev_probs[k]
+                    g = 2.0 * (x - T(host_probs[k].target))
+                    nys.nys_adjoint(h, pr[0], pr[3], x, y, z, info, g, eta=1e-10)
+                    out.append(info)
+                return out
             out = []
             for pr in dev_probs:
                 x, y, z, info = nys.nys_solve(h, *pr[:4], *start(pr), **(pr[8] if len(pr) > 8 else {}))
@@ -414,8 +423,8 @@ def main():
         barrier()
         torch.cuda.synchronize(dev)
         launches = nys.nys_kernel_launches() - l0
-        # worker streams of the batch form are not ordered with `stream`: use the wall clock there
-        ms = t_wall * 1e3 if form == "batch" else e0.elapsed_time(e1)
+        # worker streams of the batched solves are not ordered with `stream`: use the wall clock there
+        ms = t_wall * 1e3 if form in ("batch", "diff") else e0.elapsed_time(e1)
         clocks = clk.summary()
         if world > 1:
             t = torch.tensor([ms, float(launches)], dtype=torch.float64, device=dev)
@@ -544,7 +553,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
                        "start": "practical initial point" if args.practical_start else "workload interior point",
-                       "max_batch": args.max_batch if form == "batch" else None,
+                       "max_batch": args.max_batch if form in ("batch", "diff") else None,
                        "reuse_pcg": args.reuse_pcg,
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6
