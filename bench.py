@@ -439,8 +439,12 @@ def main():
         A0 = dev_probs[0][0]
         m0, n0 = A0.shape
         hbm_peak, bf16_peak, peak_src = measured_peaks()
-        routes = sorted({nys.ROUTE_NAMES[nys.nys_pcg_route(h, pr[0].shape[0], pr[0].shape[1], pr[7])]
-                         for pr in dev_probs}) if form not in ("bf16", "fp8") else ["graph"]
+        if form in ("batch", "diff"):
+            # nys_solve_batched: the PCG solves of each Newton phase share cluster launches
+            routes = ["cluster (shared batch launches)"]
+        else:
+            routes = sorted({nys.ROUTE_NAMES[nys.nys_pcg_route(h, pr[0].shape[0], pr[0].shape[1], pr[7])]
+                             for pr in dev_probs}) if form not in ("bf16", "fp8") else ["graph"]
         pcg_iters = sum(i["pcg_iters_total"] for i in timed)
         pcg_s = sum(i["pcg_seconds"] for i in timed)
         pcg = {"routes": routes, "iters": pcg_iters, "device_s": pcg_s,
