@@ -292,6 +292,26 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+
+def reduce_over_ranks(ms: float, launches: int, device):
+    """Replica runs (one independent workload per rank, no data-path
+    collective): the job's time is the slowest rank's, its launches the sum."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(launches)], dtype=torch.float64, device=device)
+    tmax, tsum = t.clone(), t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), int(tsum[1])
+
+
+def job_throughput(steps: int, per_step: int, world: int, ms: float) -> float:
+    """Whole-job units per second: every rank solves `per_step` problems per
+    step (weak scaling), over the slowest rank's time."""
+    return steps * per_step * world / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def main():
@@ -427,13 +447,9 @@ def main():
         ms = t_wall * 1e3 if form in ("batch", "diff") else e0.elapsed_time(e1)
         clocks = clk.summary()
         if world > 1:
-            t = torch.tensor([ms, float(launches)], dtype=torch.float64, device=dev)
-            tmax, tsum = t.clone(), t.clone()
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-            ms, launches = float(tmax[0]), int(tsum[1])
+            ms, launches = reduce_over_ranks(ms, launches, dev)
         per_step = len(dev_probs)
-        value = args.steps * per_step * world / (ms / 1e3)
+        value = job_throughput(args.steps, per_step, world, ms)
 
         # ---- roofline of the dominant kernel
         A0 = dev_probs[0][0]
@@ -503,9 +519,7 @@ def main():
                     nys.nys_solve(h, *pr, **bx)
             e2e_s = time.perf_counter() - t0
             if world > 1:
-                te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-                dist.all_reduce(te, op=dist.ReduceOp.MAX)
-                e2e_s = float(te[0])
+                e2e_s, _ = reduce_over_ranks(e2e_s, 0, dev)
             h2d = sum(sum(t.numel() * t.element_size() for t in pr if t is not None) for pr in hp) + \
                 sum(sum(t.numel() * t.element_size() for t in bx.values()) for bx in hbox)
             d2h = sum(8 * (2 * pr[0].shape[1] + pr[0].shape[0]) for pr in hp) + \

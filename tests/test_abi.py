@@ -65,3 +65,24 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "from oracle" not in txt and "import oracle" not in txt, f
+
+
+def test_box_fields_are_checked_before_the_library_is_called():
+    """The binding rejects kinds that are not a contiguous int8 vector of
+    length n and float64 bounds of the wrong placement, without touching
+    libnys.so (marshalling only)."""
+    import torch
+    from paper_2404_14524_gb300 import nys
+    cpu = torch.device("cpu")
+    n = 5
+    kind = torch.tensor([0, 1, 2, 0, 2], dtype=torch.int8)
+    u = torch.ones(n, dtype=torch.float64)
+    f, keep = nys._box_fields(kind, u, u, None, n, cpu, True)
+    assert set(f) == {"var_kind", "u", "s0"} and len(keep) == 3
+    assert nys._box_fields(None, None, None, None, n, cpu, True) == ({}, [])
+    with pytest.raises(TypeError):
+        nys._box_fields(kind.to(torch.int32), u, u, None, n, cpu, True)
+    with pytest.raises(TypeError):
+        nys._box_fields(kind[:4], u, u, None, n, cpu, True)
+    with pytest.raises(TypeError):
+        nys._box_fields(kind, u.float(), u, None, n, cpu, True)
