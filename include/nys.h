@@ -234,8 +234,8 @@ int nys_normal_matvec_lp(nys_handle h, int m, int n, int a_dtype, const void* A,
                          const void* AT, long long ldat, const double* D, double delta, const double* v,
                          double* out);
 
-/* FP8 storage of the precision form's matrix (the brief's "FP8 with per-row
- * scales" variant of Eq. normal-eq's operator): s_r = max_c |A[r, c]| / 448
+/* FP8 storage of the precision form's matrix (the per-row-scaled FP8
+ * variant of Eq. normal-eq's operator): s_r = max_c |A[r, c]| / 448
  * (448 = the largest finite E4M3 value; s_r = 1 for an all-zero row) and
  * Q[r, c] = E4M3(A[r, c] / s_r), round to nearest, saturating, so that
  * A ~ diag(s) Q.  A: FP32 device m x n (lda >= n).  Outputs (device,

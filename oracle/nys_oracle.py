@@ -126,7 +126,7 @@ def sketch(A: np.ndarray, D: np.ndarray, Omega: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# FP8 storage of the precision form (the brief's per-row-scaled variant of the
+# FP8 storage of the precision form (a per-row-scaled variant of the
 # operator of Eq. normal-eq): E4M3 = 1 sign, 4 exponent (bias 7), 3 mantissa
 # bits, no infinities, largest finite 448, subnormal spacing 2^-9.
 # ---------------------------------------------------------------------------
