@@ -217,6 +217,47 @@ def oracle_component_times(A64, b, c, q, x0, y0, z0, ell, tol, seed, box=None):
     return t_ipm, (time.perf_counter() - t0) / k
 
 
+_SINGLE_CORE_SOLVE = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import nys_oracle as O
+d = np.load(sys.argv[2])
+cfg = json.loads(sys.argv[3])
+opt = O.Options(tol=cfg["tol"], ell=cfg["ell"], seed=cfg["seed"], reuse_pcg=cfg["reuse"])
+box = {k: d[k] for k in ("kind", "u", "s0") if k in d.files}
+t0 = time.perf_counter()
+if cfg["practical"]:
+    O.solve_from_practical_start(d["A"], d["b"], d["c"], d["q"], opt, box.get("kind"), box.get("u"))
+else:
+    O.solve(d["A"], d["b"], d["c"], d["q"], d["x0"], d["y0"], d["z0"], opt, **box)
+print(time.perf_counter() - t0)
+"""
+
+
+def oracle_single_core(p, w, seed, practical=False, reuse=0):
+    """Seconds of one whole oracle solve of problem `p` in a child process whose
+    BLAS and OpenMP pools are limited to one thread (None if it fails)."""
+    import subprocess
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "qp.npz")
+        arrays = dict(A=p["A64"], b=p["b"], c=p["c"], q=p["q"], x0=p["x0"], y0=p["y0"], z0=p["z0"])
+        if p.get("box"):
+            arrays.update(p["box"])
+        np.savez(path, **arrays)
+        cfg = json.dumps(dict(tol=w["tol"], ell=int(p["ell"]), seed=seed, reuse=reuse, practical=practical))
+        try:
+            res = subprocess.run([sys.executable, "-c", _SINGLE_CORE_SOLVE, ROOT, path, cfg], env=env,
+                                 capture_output=True, text=True, timeout=120)
+            return float(res.stdout.strip().splitlines()[-1]) if res.returncode == 0 else None
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            return None
+
+
 def cpu_baseline(problems, w, runs, seed, practical=False, reuse=0):
     """The oracle as it stands on this host's cores: a whole solve when one
     takes at most ~30 s (else timed components extrapolated with the GPU
@@ -240,8 +281,14 @@ def cpu_baseline(problems, w, runs, seed, practical=False, reuse=0):
             else:
                 O.solve(p["A64"], p["b"], p["c"], p["q"], p["x0"], p["y0"], p["z0"], opt, **(p.get("box") or {}))
         full = time.perf_counter() - t0
-        return {"value": per_step / full / per_step, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
-                "sample": f"whole oracle solve(s) of the same workload ({per_step} QP, {full:.2f} s)"}
+        out = {"value": per_step / full, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"whole oracle solve(s) of the same workload ({per_step} QP, {full:.2f} s)"}
+        one = oracle_single_core(problems[0], w, seed, practical, reuse) if est <= 15.0 else None
+        if one is not None:
+            out["single_core"] = {"value": 1.0 / one, "unit": "QP solves/s", "cores": 1,
+                                  "sample": f"one whole oracle solve with BLAS/OpenMP limited to one thread "
+                                            f"({one:.2f} s)"}
+        return out
     m, n = A64.shape
     return {"value": 1.0 / est, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
             "sample": f"1 oracle IPM iteration with PCG forced to 0 ({t_ipm:.3f} s) + 10 oracle PCG iterations "
