@@ -446,6 +446,7 @@ def main():
             h = nys.Handle(mmax, nmax, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream,
                            precision_mode={"bf16": 1, "fp8": 2}.get(form, 0),
                            start_mode=1 if args.practical_start else 0, reuse_pcg=args.reuse_pcg)
+        last_sol = {}      # the last solve's iterate (compared with the FP64 form)
         # the start point the solves receive (None: the practical start computes it)
         start = (lambda pr: pr[4:7]) if not args.practical_start else (lambda pr: (None, None, None))
 
@@ -464,6 +465,7 @@ def main():
             out = []
             for pr in dev_probs:
                 x, y, z, info = nys.nys_solve(h, *pr[:4], *start(pr), **(pr[8] if len(pr) > 8 else {}))
+                last_sol["xyz"] = (x, y, z)
                 if form == "diff":
                     g = 2.0 * (x - T(host_probs[len(out)].target))
                     nys.nys_adjoint(h, pr[0], pr[3], x, y, z, info, g, eta=1e-10)
@@ -585,11 +587,16 @@ def main():
             A64 = dev_probs[0][0].double()
             h64 = nys.Handle(m0, n0, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream)
             t0 = time.perf_counter()
-            _, _, _, i64 = nys.nys_solve(h64, A64, *dev_probs[0][1:7], check=False)
+            x64, y64, z64, i64 = nys.nys_solve(h64, A64, *dev_probs[0][1:7], check=False)
             torch.cuda.synchronize(dev)
             t64 = time.perf_counter() - t0
+            rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+            xl, yl, zl = last_sol["xyz"]
             fp64_cmp = {"value": 1.0 / t64, "unit": "QP solves/s", "status": i64["status"],
-                        "ipm_iters": i64["ipm_iters"], "pcg_iters": i64["pcg_iters_total"]}
+                        "ipm_iters": i64["ipm_iters"], "pcg_iters": i64["pcg_iters_total"],
+                        "rel_primal": i64["rel_primal"], "rel_dual": i64["rel_dual"], "mu": i64["mu"],
+                        # the precision form's answer against the FP64 form's (both stop at tol)
+                        "precision_vs_fp64": {"x": rel(xl, x64), "y": rel(yl, y64), "z": rel(zl, z64)}}
             h64.close()
             del A64
 
