@@ -366,6 +366,22 @@ def test_bad_arguments_are_rejected(nys):
     assert "bad argument" in nys.nys_last_error(h)
 
 
+def test_non_finite_input_is_reported_not_faulted(nys):
+    """A NaN in A reaches the residuals of the first iteration: the solve stops
+    with NYS_ERR_NUMERIC (arithmetic on NaN, no device fault), and the same
+    handle then solves a clean problem normally."""
+    qp = synth.workload_small(seed=9)
+    A = qp.A.copy()
+    A[3, 7] = np.nan
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=1)
+    rest = [T(v) for v in (qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0)]
+    with pytest.raises(nys.NysError) as e:
+        nys.nys_solve(h, T(A), *rest)
+    assert e.value.code == nys.NYS_ERR_NUMERIC
+    x, y, z, info = nys.nys_solve(h, T(qp.A), *rest)
+    assert info["status"] == 0 and torch.isfinite(x).all()
+
+
 def test_core_breakdown_is_reported_not_trapped(nys):
     """Omega = 0 makes Omega^T Y_nu singular: the Cholesky must report a
     breakdown status (no trap) and the handle must stay usable."""

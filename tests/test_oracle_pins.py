@@ -219,6 +219,25 @@ def test_unpreconditioned_cg_terminates_in_distinct_eigenvalue_count():
     assert res.iters == 4 and np.allclose(res.x, rhs / diag, atol=1e-12)
 
 
+def test_pcg_error_decreases_in_the_operator_norm():
+    """A textbook property of (preconditioned) CG: the error's M-norm,
+    M = N + delta I, decreases strictly at every iteration, and the iterates
+    with k forced steps are the same whatever the stopping tolerance."""
+    A, D, N = _psd_operator(12, 80, 120)
+    delta = 1e-4
+    M = N + delta * np.eye(80)
+    F = O.nystrom(A, D, O.gaussian_omega(3, 0, 80, 6))
+    rhs = np.random.default_rng(4).standard_normal(80)
+    xs = np.linalg.solve(M, rhs)
+    errs = []
+    for k in range(0, 25):
+        res = O.pcg(lambda v: O.normal_matvec(A, D, delta, v), lambda v: O.precond_inv_apply(F, delta, v),
+                    rhs, eta=0.0, maxit=1000, forced_iters=k)
+        e = res.x - xs
+        errs.append(float(np.sqrt(e @ M @ e)))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
 def test_pcg_zero_rhs():
     res = O.pcg(lambda v: 2 * v, lambda v: v, np.zeros(5), eta=1e-8, maxit=10)
     assert res.iters == 0 and np.all(res.x == 0)
