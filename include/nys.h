@@ -50,7 +50,8 @@ typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2, NYS_FP8E4M3 = 3 } nys_dty
 
 /* Solver options.  Defaults (nys_default_options): tol 1e-6, ell 20,
  * max_ipm_iter 200, max_pcg_iter 1000, seed 0, rho0 = delta0 = 8 (Algorithm 6,
- * second step), reg_floor 5e-10 (the floor seen in Tables 7-8). */
+ * second step), reg_floor 5e-10 (the floor seen in Tables 7-8), no forced
+ * counts, start_mode 0, reuse_pcg 0. */
 typedef struct {
     double tol;                   /* relative KKT tolerance of the termination test  */
     int ell;                      /* Nystrom sketch size (clamped to m)               */
@@ -91,7 +92,7 @@ typedef struct {
 /* One QP.  With host == 0 all pointers are device pointers; with host == 1
  * they are host pointers and nys_solve stages them to the device itself
  * (copies included in nys_result.seconds).  x0, y0, z0 is the strictly
- * interior start point (x0 > 0, z0 > 0).
+ * interior start point (x0 > 0, z0 > 0; unused with options.start_mode 1).
  * Warm start (resume from a saved state): lam0 and zeta0 are the PMM
  * estimates lambda, zeta (NULL = y0, x0 as in Algorithm 6), the options'
  * rho0/delta0 carry rho and delta, and k0 is the index of the first IPM
@@ -139,8 +140,8 @@ typedef struct {
     int pcg_iters_total;
     int refine_steps;
     double rel_primal;            /* ||Ax - b|| / (1 + ||b||)  ((P~): see var_kind)    */
-    double rel_dual;              /* ||c + Qx - A^T y - z|| / (1 + ||c||)              */
-    double mu;                    /* x^T z / n                                         */
+    double rel_dual;              /* ||c + Qx - A^T y - z (+ s)|| / (1 + ||c||)        */
+    double mu;                    /* x^T z / n  ((P~): see var_kind)                   */
     double rel_gap;               /* |pobj - dobj| / (1 + |pobj|)                      */
     double rho, delta;            /* final PMM regularisation                          */
     double seconds;               /* wall time inside nys_solve                        */
