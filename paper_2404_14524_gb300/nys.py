@@ -475,6 +475,23 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     return x, y, z, info
 
 
+def solve(A, b, c, q, x0=None, y0=None, z0=None, ell: int = 20, tol: float = 1e-6, kind=None, u=None,
+          s0=None, w0=None, **options):
+    """One call: a handle sized for A (start_mode 1, the practical initial
+    point, when no x0 is given), nys_solve, and the handle released again.
+    Tensors as for nys_solve; other keyword arguments are nys_options fields
+    (seed, max_ipm_iter, max_pcg_iter, precision_mode, reuse_pcg, ...).
+    Returns (x, y, z, info)."""
+    m, n = A.shape
+    if x0 is None:
+        options.setdefault("start_mode", 1)
+    h = Handle(m, n, ell=ell, tol=tol, **options)
+    try:
+        return nys_solve(h, A, b, c, q, x0, y0, z0, kind=kind, u=u, s0=s0, w0=w0)
+    finally:
+        h.close()
+
+
 def nys_adjoint(h: Handle, A, q, x, y, z, info, dL_dx, eta: float = 1e-12):
     """Gradients of L(x*) for one solved QP (device FP64 tensors; `info` is the
     dict returned by nys_solve).  Returns dict(c=..., b=..., q=..., A=...)."""

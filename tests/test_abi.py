@@ -86,3 +86,37 @@ def test_box_fields_are_checked_before_the_library_is_called():
         nys._box_fields(kind[:4], u, u, None, n, cpu, True)
     with pytest.raises(TypeError):
         nys._box_fields(kind, u.float(), u, None, n, cpu, True)
+
+
+def test_one_call_solve_sizes_a_handle_and_releases_it(monkeypatch):
+    """nys.solve: a handle of A's size, the practical start when no x0 is given,
+    nys_solve with the same tensors, and the handle closed afterwards (the
+    library itself is replaced by fakes: marshalling only)."""
+    import torch
+    from paper_2404_14524_gb300 import nys
+    made, calls = [], []
+
+    class FakeHandle:
+        def __init__(self, m, n, **kw):
+            self.m, self.n, self.kw, self.closed = m, n, kw, False
+            made.append(self)
+
+        def close(self):
+            self.closed = True
+
+    def fake_solve(h, A, b, c, q, x0, y0, z0, **kw):
+        calls.append((h, x0, kw))
+        return "x", "y", "z", {"status": 0}
+
+    monkeypatch.setattr(nys, "Handle", FakeHandle)
+    monkeypatch.setattr(nys, "nys_solve", fake_solve)
+    A = torch.zeros(3, 7, dtype=torch.float64)
+    v = torch.zeros(7, dtype=torch.float64)
+    out = nys.solve(A, torch.zeros(3, dtype=torch.float64), v, v, ell=2, tol=1e-8, reuse_pcg=5)
+    assert out[3]["status"] == 0
+    h = made[0]
+    assert (h.m, h.n) == (3, 7) and h.closed
+    assert h.kw == {"ell": 2, "tol": 1e-8, "reuse_pcg": 5, "start_mode": 1}
+    assert calls[0][1] is None and calls[0][2]["kind"] is None
+    nys.solve(A, torch.zeros(3, dtype=torch.float64), v, v, x0=v, y0=torch.zeros(3, dtype=torch.float64), z0=v)
+    assert "start_mode" not in made[1].kw and made[1].closed
