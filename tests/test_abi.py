@@ -120,3 +120,55 @@ def test_one_call_solve_sizes_a_handle_and_releases_it(monkeypatch):
     assert calls[0][1] is None and calls[0][2]["kind"] is None
     nys.solve(A, torch.zeros(3, dtype=torch.float64), v, v, x0=v, y0=torch.zeros(3, dtype=torch.float64), z0=v)
     assert "start_mode" not in made[1].kw and made[1].closed
+
+
+def test_plain_c_program_links_and_gets_argument_errors(libpath):
+    """A C program built against include/nys.h and linked with libnys.so:
+    defaults as documented, invalid arguments rejected with NYS_ERR_ARG before
+    any device work, and nys_create either succeeds (a GPU is present: the
+    handle is destroyed again) or reports NYS_ERR_CUDA (no GPU) -- never a crash."""
+    import subprocess
+    import tempfile
+    src = r'''
+#include "nys.h"
+#include <stdio.h>
+int main(void) {
+  nys_options o;
+  nys_default_options(&o);
+  printf("%g %d %d %d %g %g %d %d %d\n", o.tol, o.ell, o.max_ipm_iter, o.max_pcg_iter, o.rho0, o.reg_floor,
+         o.forced_ipm_iters, o.start_mode, o.reuse_pcg);
+  nys_handle h = 0;
+  printf("%d %d %d\n", nys_create(0, &o, 10, 20, 0, 0), nys_create(&h, &o, 0, 20, 0, 0),
+         nys_create(&h, 0, 10, 20, 0, 0));
+  o.precision_mode = 3;
+  printf("%d\n", nys_create(&h, &o, 10, 20, 0, 0));
+  o.precision_mode = 0;
+  int rc = nys_create(&h, &o, 10, 20, 0, 0);
+  printf("%d\n", rc);
+  if (rc == NYS_OK) {
+    nys_problem p = {0};
+    nys_result r = {0};
+    printf("%d\n", nys_solve(h, &p, &r));    /* m = n = 0: rejected */
+    nys_destroy(h);
+  } else {
+    printf("%d\n", NYS_ERR_ARG);
+  }
+  return 0;
+}
+'''
+    libdir = os.path.dirname(libpath)
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(B.nvcc())), "lib64")
+    env = dict(os.environ, LD_LIBRARY_PATH=os.pathsep.join([libdir, cuda_lib, os.environ.get("LD_LIBRARY_PATH", "")]))
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe, "-L", libdir, "-lnys",
+                        "-Wl,-rpath," + libdir], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True, env=env, timeout=120).stdout
+    lines = out.split("\n")
+    assert lines[0].split() == ["1e-06", "20", "200", "1000", "8", "5e-10", "-1", "0", "0"]
+    assert lines[1].split() == ["-1", "-1", "-1"]
+    assert lines[2] == "-1"
+    assert lines[3] in ("0", "-2")
+    assert lines[4] == "-1"
