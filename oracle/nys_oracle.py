@@ -404,6 +404,7 @@ class IterRecord:
     pcg_corr: int
     state: tuple | None = None
     reused: bool = False         # the Nystrom factor of the previous iteration was kept
+    ref: tuple | None = None     # (ref_p, ref_d) of the PEU at the top of this iteration (record=True)
 
 
 @dataclasses.dataclass
@@ -423,6 +424,72 @@ class Result:
     trace: list
     w: np.ndarray | None = None     # slack u - x and its dual (box-constrained
     s: np.ndarray | None = None     #   variables; zero outside J)
+    lam: np.ndarray | None = None   # PMM estimates and PEU references after the last update
+    zeta: np.ndarray | None = None
+    ref_p: float = float("nan")
+    ref_d: float = float("nan")
+
+
+# ---------------------------------------------------------------------------
+# PMM parameter update (Algorithm 6, last step).
+#
+# The paper takes this step from Pougkakiotis-Gondzio's PEU without restating
+# it; what it does fix is the outcome: rho_0 = delta_0 = 8, the two parameters
+# move independently of each other, and neither goes below 5e-10 (the traces
+# of Tables 7-8).  Between two consecutive rows of those tables each
+# parameter shrinks by one of two factors, 1 - r or 1 - (2/3) r, with r the
+# same for both (tests/golden/peu_tables.txt checks every row pair).
+# READING, in the spirit of the method of multipliers: the multiplier
+# estimate lambda and its penalty delta belong to the primal constraint
+# Ax = b, the proximal centre zeta and its weight rho to the dual one.  An
+# estimate is re-centred on the new iterate (lambda <- y, zeta <- x) when its
+# infeasibility made enough progress, and then its parameter takes the larger
+# cut (1 - r); otherwise the estimate stays and the parameter takes the
+# smaller cut (1 - (2/3) r).  r = |mu_{k+1} - mu_k| / max(mu_k, mu_{k+1}).
+# ---------------------------------------------------------------------------
+
+PEU_PROGRESS = 0.95      # READING: an infeasibility made progress when it fell to 95% of its reference
+PEU_SLOW_CUT = 2.0 / 3.0  # Tables 7-8: the other parameter shrinks by 1 - (2/3) r
+
+
+@dataclasses.dataclass
+class PMM:
+    """PMM subproblem parameters lambda^k, zeta^k, rho_k, delta_k with the
+    relative primal / dual infeasibility recorded at the last re-centring of
+    lambda / zeta (ref_p / ref_d)."""
+    lam: np.ndarray
+    zeta: np.ndarray
+    rho: float
+    delta: float
+    ref_p: float
+    ref_d: float
+
+
+def peu_progress(rel_new: float, ref: float, tol: float) -> bool:
+    """READING: progress means the relative infeasibility fell to
+    PEU_PROGRESS times its reference or meets the termination tolerance.  An
+    estimate whose reference already met the tolerance (a feasible start,
+    where it is zero) always counts as progressing: without that clause it
+    could not be re-centred before the solve ends."""
+    return ref <= tol or rel_new <= max(PEU_PROGRESS * ref, tol)
+
+
+def peu_update(pmm: PMM, x: np.ndarray, y: np.ndarray, mu_old: float, mu_new: float,
+               rel_p: float, rel_d: float, tol: float, floor: float) -> PMM:
+    """One PMM parameter update (see the block comment above): rel_p, rel_d
+    are the relative infeasibilities (kkt_measures) of the new iterate x, y."""
+    den = max(mu_old, mu_new)
+    r = abs(mu_new - mu_old) / den if den > 0.0 else 0.0
+    if peu_progress(rel_p, pmm.ref_p, tol):
+        lam, ref_p, delta = y.copy(), rel_p, (1.0 - r) * pmm.delta
+    else:
+        lam, ref_p, delta = pmm.lam, pmm.ref_p, (1.0 - PEU_SLOW_CUT * r) * pmm.delta
+    if peu_progress(rel_d, pmm.ref_d, tol):
+        zeta, ref_d, rho = x.copy(), rel_d, (1.0 - r) * pmm.rho
+    else:
+        zeta, ref_d, rho = pmm.zeta, pmm.ref_d, (1.0 - PEU_SLOW_CUT * r) * pmm.rho
+    return PMM(lam=lam, zeta=zeta, rho=max(floor, rho), delta=max(floor, delta),
+               ref_p=ref_p, ref_d=ref_d)
 
 
 def kkt_measures(A, b, c, q, x, y, z, kind=None, u=None, w=None, s=None):
@@ -458,7 +525,8 @@ def duality_gap(b, c, q, x, y, kind=None, u=None, s=None):
 
 
 def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int = 0,
-          record: bool = False, kind=None, u=None, s0=None, w0=None) -> Result:
+          record: bool = False, kind=None, u=None, s0=None, w0=None,
+          ref_p0: float | None = None, ref_d0: float | None = None) -> Result:
     """Nys-IP-PMM from a given strictly interior start (Algorithm 6).
 
     READING (start): the workloads supply a strictly feasible interior point
@@ -468,15 +536,11 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     opt.delta0 carry the PMM parameters, and k0 is the index of the first IPM
     iteration (it selects Omega_k).  With record=True every trace entry also
     holds the state (x, y, z, lambda, zeta) at the top of its iteration
-    (followed by w, s for problems with box-constrained variables).
-    READING (PEU, which the paper only cites): after every iteration the
-    estimates follow the iterate, lambda <- y and zeta <- x (the proximal
-    centres are re-centred), and both regularisation parameters decay with
-    the relative change of mu: with r_mu = |mu_{k+1} - mu_k| / max(mu_k,
-    mu_{k+1}), rho <- max(floor, (1 - r_mu) rho), delta <- max(floor,
-    (1 - r_mu) delta).  (Keeping the estimates fixed until the infeasibility
-    drops by 5% never re-centres them from a feasible start, where the
-    infeasibility starts at zero, and costs 1.5-2x more IPM iterations.)
+    (followed by w, s for problems with box-constrained variables) and
+    `ref` the pair (ref_p, ref_d) in force there.
+    The PMM parameters follow peu_update() after every iteration.  A resumed
+    solve also takes ref_p0, ref_d0: the relative infeasibilities at the last
+    re-centring of lambda and zeta (default: those of the start point).
 
     Free and box-constrained variables (problems (P~)/(D~)): `kind` holds
     KIND_I, KIND_F or KIND_J per variable, u the upper bounds (read on J
@@ -500,6 +564,10 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     lam_pmm = y.copy() if lam0 is None else np.asarray(lam0, dtype=np.float64).copy()
     zeta = x.copy() if zeta0 is None else np.asarray(zeta0, dtype=np.float64).copy()
     rho, delta = opt.rho0, opt.delta0
+    rel_p0, rel_d0, _ = kkt_measures(A, b, c, q, x, y, z, kind, u, w, s)
+    pmm = PMM(lam=lam_pmm, zeta=zeta, rho=rho, delta=delta,
+              ref_p=rel_p0 if ref_p0 is None else float(ref_p0),
+              ref_d=rel_d0 if ref_d0 is None else float(ref_d0))
     ell = min(opt.ell, m)
     trace, pcg_counts = [], []
     status = "max_iter"
@@ -517,7 +585,8 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
             break
         if k >= opt.max_ipm_iter:
             break
-        state_lam, state_zeta = lam_pmm.copy(), zeta.copy()
+        lam_pmm, zeta, rho, delta = pmm.lam, pmm.zeta, pmm.rho, pmm.delta
+        state_lam, state_zeta, state_ref = lam_pmm.copy(), zeta.copy(), (pmm.ref_p, pmm.ref_d)
         x_top, y_top, z_top = x.copy(), y.copy(), z.copy()
         w_top, s_top = (w.copy(), s.copy()) if box else (None, None)
         D = scaling_D(x, z, q, rho, kind, w, s)
@@ -585,19 +654,17 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
             rec.state = (x_top, y_top, z_top, state_lam, state_zeta)
             if box:
                 rec.state += (w_top, s_top)
+            rec.ref = state_ref
         trace.append(rec)
-        # PEU (READING, see docstring).
-        den = max(mu, mu_new)
-        r_mu = abs(mu_new - mu) / den if den > 0.0 else 0.0
-        lam_pmm = y.copy()
-        zeta = x.copy()
-        delta = max(opt.reg_floor, (1.0 - r_mu) * delta)
-        rho = max(opt.reg_floor, (1.0 - r_mu) * rho)
+        # Algorithm 6, last step: PMM parameters of the next subproblem.
+        rel_p_new, rel_d_new, _ = kkt_measures(A, b, c, q, x, y, z, kind, u, w, s)
+        pmm = peu_update(pmm, x, y, mu, mu_new, rel_p_new, rel_d_new, opt.tol, opt.reg_floor)
         mu = mu_new
         k += 1
     return Result(x=x, y=y, z=z, status=status, ipm_iters=k, pcg_iters=pcg_counts,
                   rel_p=rel_p, rel_d=rel_d, mu=mu, rel_gap=duality_gap(b, c, q, x, y, kind, u, s),
-                  rho=rho, delta=delta, trace=trace, w=w, s=s)
+                  rho=pmm.rho, delta=pmm.delta, trace=trace, w=w, s=s,
+                  lam=pmm.lam, zeta=pmm.zeta, ref_p=pmm.ref_p, ref_d=pmm.ref_d)
 
 
 # ---------------------------------------------------------------------------
