@@ -95,8 +95,20 @@ typedef struct {
  * interior start point (x0 > 0, z0 > 0; unused with options.start_mode 1).
  * Warm start (resume from a saved state): lam0 and zeta0 are the PMM
  * estimates lambda, zeta (NULL = y0, x0 as in Algorithm 6), the options'
- * rho0/delta0 carry rho and delta, and k0 is the index of the first IPM
- * iteration (it selects the Gaussian test matrix Omega_k). */
+ * rho0/delta0 carry rho and delta, k0 is the index of the first IPM
+ * iteration (it selects the Gaussian test matrix Omega_k), and with
+ * has_peu_ref = 1 peu_ref_p / peu_ref_d are the relative primal / dual
+ * infeasibilities recorded at the last re-centring of lambda / zeta
+ * (has_peu_ref = 0: those of the start point, as in a fresh solve).
+ *
+ * PMM parameter update (Algorithm 6, last step; the paper fixes its outcome
+ * in Tables 7-8: rho_0 = delta_0 = 8, independent decrease, floor 5e-10):
+ * after each iteration r = |mu_new - mu_old| / max(mu_new, mu_old); lambda is
+ * re-centred on y and delta shrinks by 1 - r when the relative primal
+ * infeasibility fell to 95% of its value at lambda's last re-centring (or
+ * meets tol, or that value already met tol), else delta shrinks by
+ * 1 - (2/3) r and lambda stays; zeta, rho likewise with the dual
+ * infeasibility and x.  Both parameters are floored at reg_floor. */
 typedef struct {
     int m, n;
     int a_dtype;                  /* nys_dtype of A                                   */
@@ -125,6 +137,16 @@ typedef struct {
     const double* u;              /* n: upper bounds (read on J)                      */
     const double* w0;             /* n: start of w on J (NULL = u - x0)               */
     const double* s0;             /* n: start of s on J                               */
+    int has_peu_ref;              /* 1: peu_ref_p, peu_ref_d below are used (resume)  */
+    double peu_ref_p, peu_ref_d;
+    /* Parity mode for this problem alone (optional): with forced_override = 1
+     * these replace the options' forced_pcg_iters / n_forced_pcg /
+     * forced_ipm_iters (same meaning; host array), so that each problem of a
+     * batch can follow its own recorded counts. */
+    int forced_override;
+    const int* forced_pcg_iters;
+    int n_forced_pcg;
+    int forced_ipm_iters;
 } nys_problem;
 
 /* Result.  x, y, z are caller-allocated outputs (n, m, n) in the same memory
@@ -155,6 +177,8 @@ typedef struct {
     double *w, *s;                /* n each, NULL = not wanted: final slack and bound */
                                   /*   multiplier of a (P~) problem (0 outside J)     */
     int sketches;                 /* Nystrom factors built (= ipm_iters unless reused) */
+    double peu_ref_p, peu_ref_d;  /* final references of the PMM update (resumable    */
+                                  /*   state together with lam, zeta, rho, delta)      */
 } nys_result;
 
 /* Fill *opt with the defaults listed above. */
@@ -264,6 +288,8 @@ int nys_normal_matvec_fp8(nys_handle h, int m, int n, const void* Q, long long l
  * GPU that loads it until exit; n <= 1,048,576 (larger n returns
  * NYS_ERR_NOMEM).  The first call on a device, with that device current,
  * looks up the array's device address (make it before any stream capture).
+ * The address is cached per device for the life of the process: after a
+ * cudaDeviceReset of that device no further call may be made.
  * All calls share the array: calls that may overlap on the GPU race and must
  * be serialised by the caller.  A: FP64 row-major m x n (lda >= n); D: n;
  * v, out: m (out must not alias v); all device pointers; work is issued on

@@ -748,6 +748,10 @@ struct IpmRun {
   const double *b = nullptr, *c = nullptr, *q = nullptr;
   double bnorm = 0.0, cnorm = 0.0, rho = 0.0, delta = 0.0, mu = 0.0, mu_prev = 0.0;
   double rel_p = 0.0, rel_d = 0.0, eta = 0.0, t_pre = 0.0;
+  // PMM parameter update: relative primal / dual infeasibility at the last
+  // re-centring of lambda / zeta (negative until the first iteration's top
+  // sets them, unless a resumed problem supplies them)
+  double ref_p = -1.0, ref_d = -1.0;
   // problem (P~): free and box-constrained variables present
   bool box = false;
   double n_mu = 0.0;            // |I u J| + |J|, the divisor of mu
@@ -761,9 +765,12 @@ struct IpmRun {
 
   int next_forced() {
     const nys_options& o = h->opt;
-    if (o.forced_pcg_iters && forced_idx < o.n_forced_pcg) return o.forced_pcg_iters[forced_idx++];
+    const int* f = p->forced_override ? p->forced_pcg_iters : o.forced_pcg_iters;
+    const int nf = p->forced_override ? p->n_forced_pcg : o.n_forced_pcg;
+    if (f && forced_idx < nf) return f[forced_idx++];
     return -1;
   }
+  int forced_ipm() const { return p->forced_override ? p->forced_ipm_iters : h->opt.forced_ipm_iters; }
   void log_pcg(int it) {
     r->pcg_iters_total += it;
     if (r->pcg_log && r->pcg_log_len < r->pcg_log_cap) r->pcg_log[r->pcg_log_len++] = it;
@@ -925,6 +932,8 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   else CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
   rho = o.rho0;
   delta = o.delta0;
+  ref_p = p->has_peu_ref ? p->peu_ref_p : -1.0;
+  ref_d = p->has_peu_ref ? p->peu_ref_d : -1.0;
   status = NYS_WARN_MAXITER;
   done = false;
   return NYS_OK;
@@ -1044,22 +1053,42 @@ int IpmRun::top() {
   }
   rel_p = nrp / (1.0 + pnorm);
   rel_d = nrd / (1.0 + cnorm);
+  if (ref_p < 0.0) ref_p = rel_p;     // the start point's infeasibilities
+  if (ref_d < 0.0) ref_d = rel_d;
   if (k > 0) {
-    // PMM parameter update (reading of PEU): re-centre the proximal
-    // estimates on the iterate and decay rho, delta with the change of mu.
+    // PMM parameter update (Algorithm 6, last step; the paper fixes only its
+    // outcome, Tables 7-8).  Each estimate is re-centred on the iterate when
+    // its infeasibility progressed (fell to 95% of the value at its last
+    // re-centring, or meets tol, or that value already met tol) and its
+    // parameter then shrinks by 1 - r; otherwise the estimate stays and the
+    // parameter shrinks by 1 - (2/3) r.  lambda, delta follow the primal
+    // infeasibility, zeta, rho the dual one; r = |mu_k - mu_{k-1}| / max.
     const double den = std::max(mu_prev, mu);
     const double r_mu = den > 0.0 ? std::fabs(mu - mu_prev) / den : 0.0;
-    CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-    delta = std::max(o.reg_floor, (1.0 - r_mu) * delta);
-    rho = std::max(o.reg_floor, (1.0 - r_mu) * rho);
+    const double slow = 1.0 - (2.0 / 3.0) * r_mu;
+    if (ref_p <= o.tol || rel_p <= std::max(0.95 * ref_p, o.tol)) {
+      CK(cudaMemcpyAsync(h->lam, h->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+      ref_p = rel_p;
+      delta = (1.0 - r_mu) * delta;
+    } else {
+      delta = slow * delta;
+    }
+    if (ref_d <= o.tol || rel_d <= std::max(0.95 * ref_d, o.tol)) {
+      CK(cudaMemcpyAsync(h->zeta, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      ref_d = rel_d;
+      rho = (1.0 - r_mu) * rho;
+    } else {
+      rho = slow * rho;
+    }
+    delta = std::max(o.reg_floor, delta);
+    rho = std::max(o.reg_floor, rho);
     // predictor right-hand sides with the updated PMM parameters
     rc = residuals();
     if (rc != NYS_OK) { stop(rc); return rc; }
   }
   // Termination (reading of TC: relative infeasibilities and mu).
-  if (o.forced_ipm_iters >= 0) {
-    if (k >= o.forced_ipm_iters) {
+  if (forced_ipm() >= 0) {
+    if (k >= forced_ipm()) {
       stop((rel_p <= o.tol && rel_d <= o.tol && mu <= o.tol) ? NYS_OK : NYS_WARN_MAXITER);
       return NYS_OK;
     }
@@ -1222,6 +1251,8 @@ int IpmRun::finish() {
   r->rel_gap = std::fabs(pobj - dobj) / (1.0 + std::fabs(pobj));
   r->rho = rho;
   r->delta = delta;
+  r->peu_ref_p = ref_p;
+  r->peu_ref_d = ref_d;
   if (status == NYS_OK && warn != NYS_OK) status = warn;
   if (status >= 0 && rc2 != NYS_OK) status = rc2;
   if (status >= 0 && h->h_red[7] != 0.0) status = fail(h, NYS_ERR_NUMERIC, "non-finite final iterate");

@@ -57,7 +57,10 @@ class Problem(ctypes.Structure):
                 ("host", ctypes.c_int), ("lam0", ctypes.c_void_p), ("zeta0", ctypes.c_void_p),
                 ("k0", ctypes.c_int), ("ell", ctypes.c_int),
                 ("var_kind", ctypes.c_void_p), ("u", ctypes.c_void_p), ("w0", ctypes.c_void_p),
-                ("s0", ctypes.c_void_p)]
+                ("s0", ctypes.c_void_p), ("has_peu_ref", ctypes.c_int), ("peu_ref_p", ctypes.c_double),
+                ("peu_ref_d", ctypes.c_double), ("forced_override", ctypes.c_int),
+                ("forced_pcg_iters", ctypes.POINTER(ctypes.c_int)), ("n_forced_pcg", ctypes.c_int),
+                ("forced_ipm_iters", ctypes.c_int)]
 
 # variable kinds of problems (P~)/(D~) (Problem.var_kind)
 KIND_I, KIND_F, KIND_J = 0, 1, 2
@@ -73,7 +76,7 @@ class Result(ctypes.Structure):
                 ("delta", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("pcg_seconds", ctypes.c_double), ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
                 ("pcg_log_len", ctypes.c_int), ("w", ctypes.c_void_p), ("s", ctypes.c_void_p),
-                ("sketches", ctypes.c_int)]
+                ("sketches", ctypes.c_int), ("peu_ref_p", ctypes.c_double), ("peu_ref_d", ctypes.c_double)]
 
 
 _lib = None
@@ -417,11 +420,12 @@ def _box_fields(kind, u, s0, w0, n, dev, host):
 
 def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check: bool = True,
               lam0=None, zeta0=None, k0: int = 0, want_pmm: bool = False, kind=None, u=None,
-              s0=None, w0=None):
+              s0=None, w0=None, peu_ref=None):
     """Solve one QP.  CUDA tensors -> device problem; CPU tensors -> host
     problem (the library stages the data; pin the tensors for fast copies).
     lam0/zeta0/k0 resume from a saved state (rho/delta come from the handle's
-    options).  kind (int8: KIND_I, KIND_F, KIND_J per variable), u, s0 and
+    options; peu_ref = (ref_p, ref_d) are the PMM update's references,
+    None = those of the start point).  kind (int8: KIND_I, KIND_F, KIND_J per variable), u, s0 and
     optionally w0 make it problem (P~) with free and box-constrained
     variables; info then also holds the final w and s.  With a handle
     created with start_mode=1 (the practical initial point) x0, y0, z0, s0
@@ -454,6 +458,8 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
                 z0=opt_ptr(z0), host=1 if host else 0,
                 lam0=lam0.data_ptr() if lam0 is not None else None,
                 zeta0=zeta0.data_ptr() if zeta0 is not None else None, k0=k0, **bf)
+    if peu_ref is not None:
+        p.has_peu_ref, p.peu_ref_p, p.peu_ref_d = 1, float(peu_ref[0]), float(peu_ref[1])
     log = (ctypes.c_int * pcg_log_cap)()
     w, s = (mk(n), mk(n)) if kind is not None else (None, None)
     r = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr(),
@@ -466,7 +472,8 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
         h.check(rc)
     info = {k: getattr(r, k) for k in ("status", "ipm_iters", "pcg_iters_total", "refine_steps",
                                        "rel_primal", "rel_dual", "mu", "rel_gap", "rho", "delta",
-                                       "seconds", "pcg_seconds", "sketches")}
+                                       "seconds", "pcg_seconds", "sketches", "peu_ref_p",
+                                       "peu_ref_d")}
     info["pcg_log"] = list(log[: r.pcg_log_len])
     if want_pmm:
         info["lam"], info["zeta"] = lam, zeta
@@ -481,8 +488,12 @@ def solve(A, b, c, q, x0=None, y0=None, z0=None, ell: int = 20, tol: float = 1e-
     point, when no x0 is given), nys_solve, and the handle released again.
     Tensors as for nys_solve; other keyword arguments are nys_options fields
     (seed, max_ipm_iter, max_pcg_iter, precision_mode, reuse_pcg, ...).
-    Returns (x, y, z, info)."""
+    x0, y0, z0 are given together or not at all; under start_mode=1 any
+    given start is ignored.  Returns (x, y, z, info)."""
     m, n = A.shape
+    given = [t is not None for t in (x0, y0, z0)]
+    if any(given) and not all(given):
+        raise ValueError("x0, y0 and z0 must be given together (or all None for the practical start)")
     if x0 is None:
         options.setdefault("start_mode", 1)
     h = Handle(m, n, ell=ell, tol=tol, **options)
@@ -536,16 +547,19 @@ def qp_solve(A, b, c, q, x0, y0, z0, handle, eta: float = 1e-12):
     return NysQPFunction.apply(A, b, c, q, x0, y0, z0, handle, eta)
 
 
-def nys_solve_batched(h: Handle, problems, check: bool = True):
+def nys_solve_batched(h: Handle, problems, check: bool = True, forced=None, pcg_log_cap: int = 4096):
     """Solve a list of QPs [(A, b, c, q, x0, y0, z0[, ell[, box]]), ...]
     (device tensors; optional per-problem sketch size, 0 = the handle's; box
     = dict(kind=, u=, s0=[, w0=]) for a problem (P~)) in one call; the handle
-    must have max_batch >= 1.  Returns a list of (x, y, z, info); info holds
-    w and s for the (P~) problems."""
+    must have max_batch >= 1.  forced: optional per-problem parity counts,
+    a list of (pcg_counts, ipm_iters) or None entries.  Returns a list of
+    (x, y, z, info); info holds the PCG log, and w and s for the (P~)
+    problems."""
     k = len(problems)
     P = (Problem * k)()
     R = (Result * k)()
     outs, keep = [], []
+    logs = [(ctypes.c_int * pcg_log_cap)() for _ in range(k)]
     for i, pr in enumerate(problems):
         A, b, c, q, x0, y0, z0 = pr[:7]
         ell_i = int(pr[7]) if len(pr) > 7 else 0
@@ -562,8 +576,15 @@ def nys_solve_batched(h: Handle, problems, check: bool = True):
         s = torch.empty(n, dtype=torch.float64, device=A.device) if bx else None
         P[i] = Problem(m=m, n=n, a_dtype=a_dtype, A=A.data_ptr(), lda=A.stride(0), b=b.data_ptr(), c=c.data_ptr(),
                        q=q.data_ptr(), x0=x0.data_ptr(), y0=y0.data_ptr(), z0=z0.data_ptr(), host=0, ell=ell_i, **bf)
+        if forced is not None and forced[i] is not None:
+            fp, fi = forced[i]
+            arr = (ctypes.c_int * max(1, len(fp)))(*fp)
+            keep.append(arr)
+            P[i].forced_override, P[i].forced_pcg_iters, P[i].n_forced_pcg = 1, arr, len(fp)
+            P[i].forced_ipm_iters = -1 if fi is None else int(fi)
         R[i] = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr(),
-                      w=w.data_ptr() if w is not None else None, s=s.data_ptr() if s is not None else None)
+                      w=w.data_ptr() if w is not None else None, s=s.data_ptr() if s is not None else None,
+                      pcg_log=logs[i], pcg_log_cap=pcg_log_cap)
         outs.append((x, y, z, w, s))
     rc = lib().nys_solve_batched(h.h, k, P, R)
     if check:
@@ -573,6 +594,7 @@ def nys_solve_batched(h: Handle, problems, check: bool = True):
         info = {f: getattr(R[i], f) for f in ("status", "ipm_iters", "pcg_iters_total", "refine_steps", "rel_primal",
                                               "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds",
                                               "pcg_seconds", "sketches")}
+        info["pcg_log"] = list(logs[i][: R[i].pcg_log_len])
         if w is not None:
             info["w"], info["s"] = w, s
         res.append((x, y, z, info))

@@ -53,3 +53,55 @@ def test_batched_requires_a_batch_handle(nys):
     with pytest.raises(nys.NysError) as e:
         nys.nys_solve_batched(h, [tuple(T(v) for v in (qp.A, qp.b, qp.c, qp.q, qp.x0, qp.y0, qp.z0))])
     assert "max_batch" in str(e.value)
+
+
+def _omega_response(qp, opt, rec):
+    """How far the oracle's own final iterate moves when every Omega_k is
+    perturbed by 2e-16 relative, with the iteration counts held: the rounding
+    noise floor of a whole solve on this problem."""
+    import dataclasses
+    orig = O.gaussian_omega
+
+    def pert(seed, kk, m, ell):
+        om = orig(seed, kk, m, ell)
+        return om * (1 + 2e-16 * np.sign(np.sin(np.arange(om.size))).reshape(om.shape))
+    O.gaussian_omega = pert
+    try:
+        b = O.solve_qp(qp, dataclasses.replace(opt, forced_pcg=rec.pcg_iters, forced_ipm=rec.ipm_iters))
+    finally:
+        O.gaussian_omega = orig
+    rel = lambda u, v: np.linalg.norm(u - v) / np.linalg.norm(v)
+    return max(rel(b.x, rec.x), rel(b.y, rec.y), rel(b.z, rec.z))
+
+
+def test_batched_matches_oracle_with_forced_counts(nys):
+    """QPs shaped like the 256-QP batching workload (m up to 1024, n in
+    [4m, 8m], sigma_i = 1/i, ell = min(32, m/4)) solved in one batched call,
+    each with its own recorded oracle PCG and IPM counts: every iterate
+    matches the oracle's element by element, to 1e-9 relative or 100x the
+    oracle's own rounding response where that floor is higher.  The largest
+    systems run on thread-block clusters that read A from L2."""
+    shapes = [(1024, 6144), (700, 3500), (300, 1800), (96, 500)]
+    qps = [synth.spectral_qp(5000 + m, m, n, "inv", "uniform") for m, n in shapes]
+    ells = [min(32, m // 4) for m, _ in shapes]
+    recs, floors = [], []
+    for qp, ell in zip(qps, ells):
+        opt = O.Options(ell=ell, tol=1e-6, seed=9)
+        rec = O.solve_qp(qp, opt)
+        assert rec.status == "converged"
+        recs.append(rec)
+        floors.append(_omega_response(qp, opt, rec))
+    mx, nx = max(q.m for q in qps), max(q.n for q in qps)
+    hb = nys.Handle(mx, nx, ell=32, tol=1e-6, seed=9, max_batch=len(qps))
+    probs = [tuple(T(v) for v in (q.A, q.b, q.c, q.q, q.x0, q.y0, q.z0)) + (ell,) for q, ell in zip(qps, ells)]
+    res = nys.nys_solve_batched(hb, probs, forced=[(r.pcg_iters, r.ipm_iters) for r in recs])
+    for qp, rec, fl, (x, y, z, info) in zip(qps, recs, floors, res):
+        assert info["ipm_iters"] == rec.ipm_iters and info["pcg_log"] == rec.pcg_iters
+        tol = max(1e-9, 100 * fl)
+        errs = [float(np.linalg.norm(g.cpu().numpy() - w) / np.linalg.norm(w))
+                for g, w in ((x, rec.x), (y, rec.y), (z, rec.z))]
+        print(f"m={qp.m} n={qp.n} errs={errs} floor={fl:.1e}")
+        assert max(errs) <= tol
+        assert info["rel_primal"] <= 1e-6 and info["rel_dual"] <= 1e-6 and info["mu"] <= 1e-6
+        rtol = max(1e-6, 10 * tol)
+        assert info["rho"] == pytest.approx(rec.rho, rel=rtol) and info["delta"] == pytest.approx(rec.delta, rel=rtol)

@@ -63,7 +63,7 @@ def box_run():
     return qp, ref
 
 
-def _omega_sensitivity(qp, opt, state, k):
+def _omega_sensitivity(qp, opt, state, k, ref):
     """Relative move of one oracle IPM step under a 2e-16 relative perturbation
     of Omega_k (the rounding-level noise floor of that step)."""
     orig = O.gaussian_omega
@@ -72,7 +72,7 @@ def _omega_sensitivity(qp, opt, state, k):
         om = orig(seed, kk, m, ell)
         return om * (1 + 2e-16 * np.sign(np.sin(np.arange(om.size))).reshape(om.shape))
     x, y, z, lam, zeta, w, s = state
-    kw = dict(lam0=lam, zeta0=zeta, k0=k, kind=qp.kind, u=qp.u, s0=s, w0=w)
+    kw = dict(lam0=lam, zeta0=zeta, k0=k, kind=qp.kind, u=qp.u, s0=s, w0=w, ref_p0=ref[0], ref_d0=ref[1])
     a = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, **kw)
     O.gaussian_omega = pert
     try:
@@ -97,18 +97,23 @@ def test_box_single_ipm_step_matches_oracle(nys, box_run, k):
     nxt = ref.trace[k + 1] if k + 1 < len(ref.trace) else None
     want = (nxt.state[0], nxt.state[1], nxt.state[2], nxt.state[5], nxt.state[6]) if nxt is not None \
         else (ref.x, ref.y, ref.z, ref.w, ref.s)
-    floor = _omega_sensitivity(qp, opt, t.state, k)
+    floor = _omega_sensitivity(qp, opt, t.state, k, t.ref)
     tol = max(1e-9, 100 * floor)
     h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=forced, forced_ipm=1,
                    rho0=t.rho, delta0=t.delta)
-    gx, gy, gz, info = _solve(nys, h, qp, x, y, z, s0=s, w0=w, lam0=T(lam), zeta0=T(zeta), k0=k)
+    gx, gy, gz, info = _solve(nys, h, qp, x, y, z, s0=s, w0=w, lam0=T(lam), zeta0=T(zeta), k0=k,
+                              peu_ref=t.ref, want_pmm=True)
     errs = [relerr(g, v) for g, v in zip((gx, gy, gz, info["w"], info["s"]), want)]
     print(f"k={k} errs={errs} floor={floor:.2e}")
     assert max(errs) <= tol
     if nxt is not None:
-        tol_reg = 2 * tol / (nxt.rho / t.rho)
-        assert abs(info["rho"] - nxt.rho) <= tol_reg * nxt.rho
-        assert abs(info["delta"] - nxt.delta) <= tol_reg * nxt.delta
+        for got, old, new in ((info["rho"], t.rho, nxt.rho), (info["delta"], t.delta, nxt.delta)):
+            tol_reg = 2 * tol / (new / old)
+            assert abs(got - new) <= tol_reg * new
+        # the references are residual norms of the new iterate (differences of
+        # O(1) terms): they carry the iterate's error in absolute terms
+        assert (info["peu_ref_p"], info["peu_ref_d"]) == pytest.approx(nxt.ref, rel=2 * tol, abs=10 * tol)
+        assert relerr(info["lam"], nxt.state[3]) <= tol and relerr(info["zeta"], nxt.state[4]) <= tol
 
 
 def test_box_whole_solve_matches_oracle(nys, box_run):

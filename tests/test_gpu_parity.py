@@ -250,7 +250,7 @@ def test_step_length_bit_exact(nys):
 
 # ------------------------------------------------------------------ whole solve
 
-def _omega_sensitivity(qp, opt, state, k, lam, zeta):
+def _omega_sensitivity(qp, opt, state, k, lam, zeta, ref):
     """How far one oracle IPM step moves when Omega_k is perturbed by 2e-16
     relative: the rounding-level noise floor of that step (late IPM steps run
     many CG iterations on ill-conditioned systems, which amplify rounding)."""
@@ -260,10 +260,11 @@ def _omega_sensitivity(qp, opt, state, k, lam, zeta):
         om = orig(seed, kk, m, ell)
         return om * (1 + 2e-16 * np.sign(np.sin(np.arange(om.size))).reshape(om.shape))
     x, y, z = state
-    a = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, lam0=lam, zeta0=zeta, k0=k)
+    kw = dict(lam0=lam, zeta0=zeta, k0=k, ref_p0=ref[0], ref_d0=ref[1])
+    a = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, **kw)
     O.gaussian_omega = pert
     try:
-        b = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, lam0=lam, zeta0=zeta, k0=k)
+        b = O.solve(qp.A, qp.b, qp.c, qp.q, x, y, z, opt, **kw)
     finally:
         O.gaussian_omega = orig
     return max(relerr(u, v) for u, v in ((a.x, b.x), (a.y, b.y), (a.z, b.z)))
@@ -290,22 +291,30 @@ def test_single_ipm_step_matches_oracle(nys, small_run, k):
     opt = O.Options(tol=1e-6, ell=20, seed=7, rho0=t.rho, delta0=t.delta, forced_ipm=1, forced_pcg=forced)
     nxt = ref.trace[k + 1] if k + 1 < len(ref.trace) else None
     want = nxt.state[:3] if nxt is not None else (ref.x, ref.y, ref.z)
-    floor = _omega_sensitivity(qp, opt, (x, y, z), k, lam, zeta)
+    floor = _omega_sensitivity(qp, opt, (x, y, z), k, lam, zeta, t.ref)
     tol = max(1e-9, 100 * floor)
     h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=forced, forced_ipm=1,
                    rho0=t.rho, delta0=t.delta)
     gx, gy, gz, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(x), T(y), T(z),
-                                     lam0=T(lam), zeta0=T(zeta), k0=k)
+                                     lam0=T(lam), zeta0=T(zeta), k0=k, peu_ref=t.ref, want_pmm=True)
     errs = [relerr(g, w) for g, w in ((gx, want[0]), (gy, want[1]), (gz, want[2]))]
     print(f"k={k} errs={errs} floor={floor:.2e}")
     assert max(errs) <= tol
     if nxt is not None:
-        # PEU after the step: rho' = (1 - r_mu) rho with r_mu = |mu' - mu| / max(mu', mu).
-        # mu' = x'^T z' / n carries up to twice the iterate's relative error, which
-        # moves r_mu by as much in absolute terms and rho' by that over (1 - r_mu).
-        tol_reg = 2 * tol / (nxt.rho / t.rho)
-        assert abs(info["rho"] - nxt.rho) <= tol_reg * nxt.rho
-        assert abs(info["delta"] - nxt.delta) <= tol_reg * nxt.delta
+        # PMM update after the step: each parameter shrinks by 1 - r or
+        # 1 - (2/3) r with r = |mu' - mu| / max(mu', mu); mu' = x'^T z' / n
+        # carries up to twice the iterate's relative error, which moves r by
+        # as much in absolute terms and a parameter by that over its factor.
+        # Each estimate took the oracle's branch: it was re-centred (equal to
+        # the new iterate) exactly when the oracle's was, and the references
+        # moved with it.
+        for got, old, new in ((info["rho"], t.rho, nxt.rho), (info["delta"], t.delta, nxt.delta)):
+            tol_reg = 2 * tol / (new / old)
+            assert abs(got - new) <= tol_reg * new
+        # the references are residual norms of the new iterate (differences of
+        # O(1) terms): they carry the iterate's error in absolute terms
+        assert (info["peu_ref_p"], info["peu_ref_d"]) == pytest.approx(nxt.ref, rel=2 * tol, abs=10 * tol)
+        assert relerr(info["lam"], nxt.state[3]) <= tol and relerr(info["zeta"], nxt.state[4]) <= tol
 
 
 def test_small_workload_solution_matches_oracle(nys, small_run):
@@ -319,6 +328,68 @@ def test_small_workload_solution_matches_oracle(nys, small_run):
     for g, w in ((x, ref.x), (y, ref.y), (z, ref.z)):
         assert relerr(g, w) <= 1e-5
     assert info["rel_primal"] <= 1e-6 and info["rel_dual"] <= 1e-6 and info["mu"] <= 1e-6
+
+
+def _trajectory_response(qp, opt, rec):
+    """Per IPM iteration, how far the oracle's own state at the top of that
+    iteration moves when every Omega_k is perturbed by 2e-16 relative (the
+    counts held): the rounding noise floor of the trajectory up to there."""
+    import dataclasses
+    orig = O.gaussian_omega
+
+    def pert(seed, kk, m, ell):
+        om = orig(seed, kk, m, ell)
+        return om * (1 + 2e-16 * np.sign(np.sin(np.arange(om.size))).reshape(om.shape))
+    O.gaussian_omega = pert
+    try:
+        b = O.solve_qp(qp, dataclasses.replace(opt, forced_pcg=rec.pcg_iters, forced_ipm=rec.ipm_iters),
+                       record=True)
+    finally:
+        O.gaussian_omega = orig
+    per = [max(relerr(eb.state[i], ea.state[i]) for i in range(3)) for ea, eb in zip(rec.trace, b.trace)]
+    final = max(relerr(b.x, rec.x), relerr(b.y, rec.y), relerr(b.z, rec.z))
+    return per, final
+
+
+def test_whole_solve_within_1e9_on_a_well_conditioned_trajectory(nys):
+    """Differentiation-shaped QP (512 x 2048 Gaussian A, q ~ U[0.1, 1], tol
+    1e-8): the oracle's own trajectory is insensitive to rounding (its final
+    iterate moves ~1e-15 under a 2e-16 change of Omega), so the GPU's whole
+    solve, with the oracle's counts, must match the oracle's iterate to 1e-9."""
+    qp = synth.gaussian_qp(11, 512, 2048)
+    opt = O.Options(tol=1e-8, ell=32, seed=7)
+    rec = O.solve_qp(qp, opt, record=True)
+    assert rec.status == "converged"
+    per, final = _trajectory_response(qp, opt, rec)
+    assert final <= 1e-12
+    h = nys.Handle(qp.m, qp.n, ell=32, tol=1e-8, seed=7, forced_pcg=rec.pcg_iters, forced_ipm=rec.ipm_iters)
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    assert info["ipm_iters"] == rec.ipm_iters and info["pcg_log"] == rec.pcg_iters
+    errs = [relerr(g, w) for g, w in ((x, rec.x), (y, rec.y), (z, rec.z))]
+    print(f"whole solve errs={errs} oracle response={final:.1e}")
+    assert max(errs) <= 1e-9
+    assert info["rho"] == pytest.approx(rec.rho, rel=1e-9) and info["delta"] == pytest.approx(rec.delta, rel=1e-9)
+
+
+def test_small_workload_trajectory_within_1e9_while_the_oracle_is_stable(nys, small_run):
+    """m=200, n=500: the oracle's trajectory stays insensitive to rounding
+    (response <= 1e-11) for its first K iterations and then amplifies it by
+    orders of magnitude (ill-conditioned late Newton systems with forced CG
+    counts).  The GPU's first K iterations, run as one solve from the
+    workload's start with the oracle's counts, must match the oracle's state
+    at the top of iteration K to 1e-9."""
+    qp, ref = small_run
+    opt = O.Options(tol=1e-6, ell=20, seed=7)
+    per, _ = _trajectory_response(qp, opt, ref)
+    # the last top-of-iteration state whose response is still <= 1e-11
+    K = next((k for k, p in enumerate(per) if p > 1e-11), len(per)) - 1
+    assert K >= 8, per
+    h = nys.Handle(qp.m, qp.n, ell=20, tol=1e-6, seed=7, forced_pcg=ref.pcg_iters[:2 * K], forced_ipm=K)
+    x, y, z, info = nys.nys_solve(h, T(qp.A), T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    want = ref.trace[K].state if K < len(ref.trace) else (ref.x, ref.y, ref.z)
+    errs = [relerr(g, w) for g, w in zip((x, y, z), want[:3])]
+    print(f"K={K} errs={errs}")
+    assert info["ipm_iters"] == K and max(errs) <= 1e-9
 
 
 def test_free_running_solve_meets_kkt(nys):

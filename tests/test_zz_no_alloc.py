@@ -1,10 +1,14 @@
 """The allocation-free operator entry point (for callers that cannot allocate
 device memory, e.g. inside a stream capture or under a fixed memory pool)
-gives the same (N + delta I) v as the handle-based nys_normal_matvec, on two
-calls in a row through the C ABI.  Collected last on purpose."""
+gives the same (N + delta I) v as the handle-based nys_normal_matvec and as
+the CPU oracle's operator, on two calls in a row through the C ABI, including
+the largest n the fixed scratch holds (where no room is left for split
+partial sums).  Collected last on purpose."""
 import numpy as np
 import pytest
 import torch
+
+from oracle import nys_oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +41,33 @@ def test_noalloc_operator_matches_the_handle_operator_twice(nys):
         torch.cuda.synchronize()
         err = float((out - ref).abs().max() / ref.abs().max())
         assert err <= 1e-13, (call, err)
+        _check_against_oracle(A, D, delta, v, out)
+
+
+def _check_against_oracle(A, D, delta, v, out):
+    """Element by element against the oracle's FP64 operator, within the
+    rounding bound of two length-(m + n) dot-product chains."""
+    An, Dn, vn = (t.cpu().numpy() for t in (A, D, v))
+    want = O.normal_matvec(An, Dn, delta, vn)
+    m, n = An.shape
+    bound = 4 * (m + n) * 2.0 ** -53 * (np.abs(An) @ (Dn * (np.abs(An).T @ np.abs(vn))) + abs(delta) * np.abs(vn))
+    assert np.all(np.abs(out.cpu().numpy() - want) <= bound + 1e-300)
+
+
+def test_noalloc_operator_at_the_largest_n_matches_the_oracle_twice(nys):
+    """n = 2^20 fills the scratch with t alone: the entry point must fall back
+    to the unsplit A^T v pass and still agree with the oracle."""
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device="cpu").manual_seed(11)
+    m, n = 3, 1 << 20
+    A = torch.randn(m, n, generator=g, dtype=torch.float64).to(dev)
+    out = torch.empty(m, dtype=torch.float64, device=dev)
+    for call in range(2):
+        D = (torch.rand(n, generator=g, dtype=torch.float64) + 0.1).to(dev)
+        v = torch.randn(m, generator=g, dtype=torch.float64).to(dev)
+        assert nys.nys_normal_matvec_noalloc(A, D, 0.25 * (call + 1), v, out) == 0
+        torch.cuda.synchronize()
+        _check_against_oracle(A, D, 0.25 * (call + 1), v, out)
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch(nys):
