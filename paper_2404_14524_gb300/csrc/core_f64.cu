@@ -558,6 +558,144 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
   cl.sync();                             // no CTA leaves while a peer may still read its columns
 }
 
+// Mixed-precision start of the one-sided Jacobi SVD (2 <= ell <= 32).  The
+// same round-robin iteration runs first in FP32 on a copy of B (FP32
+// arithmetic is ~70x the FP64 rate on this GPU, and its roots and divisions
+// are single instructions), one warp per column pair, the rotations
+// accumulated in V (ell x ell).  V is then made orthogonal to FP64 precision
+// by two Newton-Schulz steps in FP64, X <- X (3I - X^T X) / 2 (quadratic:
+// an FP32-level defect of ~1e-6 falls below 1e-16), and written out.  B V has
+// the singular values and left singular vectors of B (V is orthogonal) and
+// nearly orthogonal columns, so the FP64 Jacobi that follows needs two or
+// three sweeps instead of six to nine.  B is scaled by a power of two so that
+// its largest column norm is about 1 (the FP32 copy keeps small columns in
+// range).  The FP32 sweeps stop when no pair needs a rotation at the FP32
+// threshold kJ32Tol or after max_sweeps.
+constexpr int kJ32T = 512;
+constexpr int kJ32W = kJ32T / 32;
+constexpr int kJ32MaxElems = 40960;      // m * ell floats of the copy (160 KB)
+constexpr float kJ32Tol = 1e-5f;
+
+__global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, const double* __restrict__ B, int ld,
+                                                            double* __restrict__ V, int max_sweeps,
+                                                            const int* err) {
+  extern __shared__ float F[];           // m x ell copy of B (column-major, ld m), then V32 (ell x ell)
+  float* V32 = F + (size_t)m * ell;
+  __shared__ double X[32 * 32], W[32 * 32];
+  __shared__ float colmax[kJ32W];
+  __shared__ int rotated;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (*err) return;
+  // power-of-two scale from the largest entry
+  float mx = 0.0f;
+  for (long long e = tid; e < (long long)m * ell; e += kJ32T) {
+    const int i = (int)(e % m), c = (int)(e / m);
+    mx = fmaxf(mx, (float)fabs(B[(size_t)c * ld + i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) colmax[wid] = mx;
+  __syncthreads();
+  mx = 0.0f;
+  for (int w = 0; w < kJ32W; ++w) mx = fmaxf(mx, colmax[w]);
+  int ex = 0;
+  if (mx > 0.0f && isfinite(mx)) frexpf(mx, &ex);
+  const double scale = ldexp(1.0, -ex);
+  for (long long e = tid; e < (long long)m * ell; e += kJ32T) {
+    const int i = (int)(e % m), c = (int)(e / m);
+    F[e] = (float)(B[(size_t)c * ld + i] * scale);
+  }
+  for (int e = tid; e < ell * ell; e += kJ32T) V32[e] = (e % ell == e / ell) ? 1.0f : 0.0f;
+  const int lp = ell + (ell & 1);
+  const int npairs = lp / 2;
+  const int L = lp - 1;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < L; ++r) {
+      if (wid < npairs) {
+        int p, q;
+        rr_pair(wid, r, lp, p, q);
+        if (q < ell) {
+          float* bp = F + (size_t)p * m;
+          float* bq = F + (size_t)q * m;
+          float al = 0.0f, be = 0.0f, ga = 0.0f;
+          for (int i = lane; i < m; i += 32) {
+            const float x = bp[i], y = bq[i];
+            al = fmaf(x, x, al);
+            be = fmaf(y, y, be);
+            ga = fmaf(x, y, ga);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          }
+          if (al > 0.0f && be > 0.0f && fabsf(ga) > kJ32Tol * sqrtf(al) * sqrtf(be)) {
+            const float d = be - al;
+            const float h = fmaf(d, d, 4.0f * ga * ga);
+            const float t = (2.0f * ga) * copysignf(1.0f, d == 0.0f ? 1.0f : d) / (fabsf(d) + sqrtf(h));
+            const float c = rsqrtf(fmaf(t, t, 1.0f));
+            const float sn = c * t;
+            for (int i = lane; i < m; i += 32) {
+              const float x = bp[i], y = bq[i];
+              bp[i] = c * x - sn * y;
+              bq[i] = sn * x + c * y;
+            }
+            if (lane < ell) {
+              float* vp = V32 + (size_t)p * ell;
+              float* vq = V32 + (size_t)q * ell;
+              const float x = vp[lane], y = vq[lane];
+              vp[lane] = c * x - sn * y;
+              vq[lane] = sn * x + c * y;
+            }
+            if (lane == 0) rotated = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();                     // everyone has read `rotated` before it is reset
+  }
+  // Newton-Schulz in FP64: X <- 1.5 X - 0.5 X (X^T X), twice
+  for (int e = tid; e < ell * ell; e += kJ32T) X[e] = (double)V32[e];
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    for (int e = tid; e < ell * ell; e += kJ32T) {          // W = X^T X, (a, b) at b * ell + a
+      const int a = e % ell, b = e / ell;
+      const double* xa = X + (size_t)a * ell;
+      const double* xb = X + (size_t)b * ell;
+      double s0 = 0.0, s1 = 0.0;
+      int k = 0;
+      for (; k + 1 < ell; k += 2) {
+        s0 = fma(xa[k], xb[k], s0);
+        s1 = fma(xa[k + 1], xb[k + 1], s1);
+      }
+      if (k < ell) s0 = fma(xa[k], xb[k], s0);
+      W[e] = s0 + s1;
+    }
+    __syncthreads();
+    double nx[2] = {0.0, 0.0};
+    for (int e = tid, u = 0; e < ell * ell; e += kJ32T, ++u) {  // (X W)(i, j) at j * ell + i
+      const int i = e % ell, j = e / ell;
+      const double* wj = W + (size_t)j * ell;
+      double s0 = 0.0, s1 = 0.0;
+      int k = 0;
+      for (; k + 1 < ell; k += 2) {
+        s0 = fma(X[(size_t)k * ell + i], wj[k], s0);
+        s1 = fma(X[(size_t)(k + 1) * ell + i], wj[k + 1], s1);
+      }
+      if (k < ell) s0 = fma(X[(size_t)k * ell + i], wj[k], s0);
+      nx[u] = fma(-0.5, s0 + s1, 1.5 * X[e]);
+    }
+    __syncthreads();
+    for (int e = tid, u = 0; e < ell * ell; e += kJ32T, ++u) X[e] = nx[u];
+    __syncthreads();
+  }
+  for (int e = tid; e < ell * ell; e += kJ32T) V[e] = X[e];
+}
+
 // G[j][j] += f * trace(G)  (one CTA): the shift of the first Cholesky-QR pass.
 __global__ void __launch_bounds__(kNT) k_shift_trace(int ell, double* G, double f) {
   __shared__ double sh[kWarps];
@@ -706,6 +844,21 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
     Jmat = cw.R;
     jm = ell;
     jld = ell;
+  }
+  if (direct && cw.f32_start && ell >= 2 && ell <= kJacobiClusterMaxEll && (long long)m * ell <= kJ32MaxElems) {
+    // FP32 Jacobi start: V (orthogonal to FP64 precision) in cw.R, then the
+    // FP64 Jacobi runs on B2 = B V
+    const size_t sm = sizeof(float) * ((size_t)m * ell + (size_t)ell * ell);
+    e = cudaFuncSetAttribute(k_jacobi_f32_start, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * (kJ32MaxElems + 32 * 32)));
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_jacobi_f32_start<<<1, kJ32T, sm, st>>>(m, ell, cw.Ynu, ld, cw.R, 12, err);
+    e = gemm_f64(st, m, ell, ell, cw.Ynu, 1, ld, cw.R, 1, ell, nullptr, cw.B2, 1, ld, cw.split_buf,
+                 cw.split_cap);
+    if (e != cudaSuccess) return e;
+    Jmat = cw.B2;
+    Bsv = cw.B2;
   }
   double tol = sqrt((double)jm) * 0x1.0p-53;
   if (tol < 0x1.0p-52) tol = 0x1.0p-52;

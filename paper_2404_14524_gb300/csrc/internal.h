@@ -96,6 +96,7 @@ struct CoreWork {
   int* sweep_flags;   // kMaxSweeps   rotation flags per Jacobi sweep
   double* split_buf;
   size_t split_cap;
+  int f32_start = 1;  // FP32 Jacobi start for small B (NYS_JACOBI_F32=0 turns it off)
   static constexpr int kMaxSweeps = 40;
 };
 // Algorithm 1 steps 3-8 from a sketch.  Writes U (m x ell, ld), lam (ell) and

@@ -1504,6 +1504,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
     if (h->pcg_path == 1) h->plan_policy = 2;
   }
   if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
+  if (const char* env = std::getenv("NYS_JACOBI_F32")) h->cw.f32_start = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess) {
     cudaFree(h->arena);

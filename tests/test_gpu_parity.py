@@ -137,6 +137,31 @@ def test_nystrom_factor_matches_oracle(nys, m, n, ell):
     assert np.linalg.norm(Nh - Nhw, 2) <= 1e-10 * np.linalg.norm(Nhw, 2)
 
 
+@pytest.mark.parametrize("f32_start", ["1", "0"])
+@pytest.mark.parametrize("m,ell,dspan", [(200, 20, 0.0), (150, 30, 12.0), (1024, 32, 6.0)])
+def test_nystrom_factor_with_and_without_the_fp32_jacobi_start(nys, monkeypatch, f32_start, m, ell, dspan):
+    """The small direct route starts the FP64 Jacobi from an FP32 Jacobi
+    rotation V (made orthogonal in FP64); either way the factor matches the
+    oracle's (D spanning up to 12 orders of magnitude, as in late IPM
+    iterations)."""
+    rng = np.random.default_rng(m + ell)
+    n = 3 * m
+    A = rng.standard_normal((m, n)) / np.sqrt(n)
+    D = 10.0 ** rng.uniform(-dspan / 2, dspan / 2, n)
+    Om = O.gaussian_omega(5, 1, m, ell)
+    Y = O.sketch(A, D, Om)
+    Fw = O.nystrom_from_sketch(Y, Om)
+    monkeypatch.setenv("NYS_JACOBI_F32", f32_start)
+    h = nys.Handle(m, n, ell=ell)
+    U, lam, nu = nys.nys_nystrom(h, P(Y), P(Om))
+    U, lam = U.cpu().numpy().T, lam.cpu().numpy()
+    assert nu == Fw.nu
+    assert np.allclose(lam, Fw.lam, rtol=1e-10, atol=1e-12 * Fw.lam[0])
+    assert np.abs(U.T @ U - np.eye(ell)).max() < 1e-12
+    Nh, Nhw = U @ np.diag(lam) @ U.T, Fw.U @ np.diag(Fw.lam) @ Fw.U.T
+    assert np.linalg.norm(Nh - Nhw, 2) <= 1e-10 * np.linalg.norm(Nhw, 2)
+
+
 def test_nystrom_exact_for_low_rank(nys):
     h, A, D, Om, Fw, U, lam, nu = _factor_pair(nys, 120, 300, 12, seed=9, rank=6)
     N = A @ (D[:, None] * A.T)
