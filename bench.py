@@ -16,8 +16,12 @@ Extra keys: `roofline` (the dominant kernel, timed with CUDA events on the
 solver's stream), `cpu_baseline` (the CPU oracle on a bounded sample, rank 0,
 N=1), `e2e` (the same solves through the C ABI with pinned host buffers,
 copies inside the timed region), `clocks` (nvidia-smi samples taken during the
-timed region) and `gpu_launches` (kernels of libnys.so launched inside the
-timed region).  `--impl reference` times the CPU oracle instead.
+timed region), `gpu_launches` (kernels of libnys.so launched inside the
+timed region) and, on one GPU, `config3`: one whole solve of the m=20000,
+n=100000, ell=400 workload in the precision form (BF16 + refinement) and in
+the FP64 form on the same QP (QP/s, counts, KKT measures, the precision form's
+distance from the FP64 form's answer; about 15 minutes, `--no-config3` skips
+it).  `--impl reference` times the CPU oracle instead.
 """
 from __future__ import annotations
 
@@ -384,6 +388,9 @@ def main():
                          "many iterations (0: a fresh sketch every iteration, Algorithm 6 as written)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision workloads: also time one FP64-form solve of the same QP")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the record of one whole m=20000, n=100000 solve in the precision and FP64 forms "
+                         "(run by default on one GPU, about 15 minutes)")
     ap.add_argument("--profile-kernel", choices=["f64_operator", "bf16_operator", "sketch_gemm", "ff_pcg", "bf16_pcg"],
                     help="run only this kernel --reps times on an m x n (x ell) case (for ncu captures)")
     ap.add_argument("--m", type=int, default=5000)
@@ -581,6 +588,9 @@ def main():
 
         # the GEMV pairs at the large workload shapes (the metric's GEMV GB/s)
         gemv = operator_rooflines(nys, dev, stream) if (rank == 0 and not args.no_gemv) else None
+        # the precision form against the FP64 form on the 20000 x 100000 workload
+        cfg3 = config3_record(nys, dev, stream, seed, cpu=not args.no_cpu_baseline) \
+            if (world == 1 and not args.no_config3 and form not in ("bf16", "fp8")) else None
 
         fp64_cmp = None
         if form in ("bf16", "fp8") and args.compare_fp64:
@@ -642,6 +652,8 @@ def main():
         line["pcg"] = pcg
         if gemv is not None:
             line["gemv"] = gemv
+        if cfg3 is not None:
+            line["config3"] = cfg3
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
@@ -742,6 +754,65 @@ def fp64_operator_roofline(nys, h, A0, stream, reps=50):
             "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (nominal FP64 1.25 TFLOP/s)",
             "hbm_gbs": bytes_alg / op_s / 1e9, "op_ms": op_s * 1e3,
             "algorithmic_flops": flops, "algorithmic_bytes": bytes_alg}
+
+
+def config3_record(nys, dev, stream, seed, cpu=True):
+    """The metric's "BF16+refine vs FP64 form" on its own configuration: one
+    whole solve of the m=20000, n=100000, ell=400, tol 1e-6 workload in the
+    precision form (BF16 inner PCG + FP32 / float-float refinement) and one in
+    the FP64 form on the same QP (the FP32 matrix defines the problem), each
+    timed from the call to its return; the precision form's answer relative to
+    the FP64 form's (the oracle cannot solve this size in bench time: its
+    per-component times on this QP, extrapolated with the GPU's counts, are
+    reported instead)."""
+    import torch
+    w = WORKLOADS["precision-20000x100000"]
+    t_all = time.perf_counter()
+    rec = {"workload": "precision-20000x100000", "desc": w["desc"]}
+    with torch.cuda.stream(stream):
+        A, b, c, q, x0, y0, z0 = device_workload(w, 0, dev)
+        m, n = A.shape
+        forms = {}
+        sols = {}
+        for name, mode in (("bf16_refine", 1), ("fp64", 0)):
+            Ause = A if mode else A.double()
+            h = nys.Handle(m, n, ell=w["ell"], tol=w["tol"], seed=seed, stream=stream, precision_mode=mode)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            x, y, z, info = nys.nys_solve(h, Ause, b, c, q, x0, y0, z0, check=False)
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter() - t0
+            h.close()
+            del Ause
+            sols[name] = (x, y, z)
+            forms[name] = {"value": 1.0 / t, "unit": "QP solves/s", "seconds": t, "status": info["status"],
+                           "ipm_iters": info["ipm_iters"], "pcg_iters": info["pcg_iters_total"],
+                           "refine_steps": info["refine_steps"], "pcg_device_s": info["pcg_seconds"],
+                           "rel_primal": info["rel_primal"], "rel_dual": info["rel_dual"], "mu": info["mu"],
+                           "rel_gap": info["rel_gap"],
+                           "kkt_met": max(info["rel_primal"], info["rel_dual"], info["mu"]) <= w["tol"]}
+        rel = lambda a, b_: float(torch.linalg.norm(a - b_) / torch.linalg.norm(b_))
+        (xb, yb, zb), (xf, yf, zf) = sols["bf16_refine"], sols["fp64"]
+        rec["forms"] = forms
+        rec["precision_vs_fp64"] = {"x": rel(xb, xf), "y": rel(yb, yf), "z": rel(zb, zf)}
+        rec["speedup_bf16_refine_over_fp64"] = forms["fp64"]["seconds"] / forms["bf16_refine"]["seconds"]
+        if cpu:
+            A64 = A.double().cpu().numpy()
+            t_ipm, t_pcg = oracle_component_times(A64, b.cpu().numpy(), c.cpu().numpy(), q.cpu().numpy(),
+                                                  x0.cpu().numpy(), y0.cpu().numpy(), z0.cpu().numpy(),
+                                                  w["ell"], w["tol"], seed)
+            del A64
+            ipm, pcg = forms["fp64"]["ipm_iters"], forms["fp64"]["pcg_iters"]
+            est = ipm * t_ipm + pcg * t_pcg
+            rec["cpu_baseline"] = {"value": 1.0 / est, "unit": "QP solves/s", "cores": os.cpu_count(),
+                                   "kind": "oracle",
+                                   "sample": f"1 oracle IPM iteration with PCG forced to 0 ({t_ipm:.1f} s) + 10 "
+                                             f"oracle PCG iterations ({t_pcg:.3f} s each) on this QP, "
+                                             f"extrapolated with the FP64 form's counts ({ipm} IPM, {pcg} PCG)"}
+        del A, b, c, q, x0, y0, z0, sols, xb, yb, zb, xf, yf, zf
+        torch.cuda.empty_cache()
+    rec["wall_s"] = time.perf_counter() - t_all
+    return rec
 
 
 def operator_rooflines(nys, dev, stream):
