@@ -385,6 +385,9 @@ class Options:
     forced_pcg: list | None = None   # per Newton solve: predictor, corrector, ...
     forced_ipm: int | None = None
     reuse_pcg: int = 0           # > 0: keep the Nystrom factor while PCG stays at or under this many iterations
+    adapt_cost: int = 0          # > 0: adaptive sketch size (sketch_size_next); the cost of a factor at
+                                 #   the largest size, in PCG iterations
+    ell_min: int = 0             # smallest adaptive sketch size (0: max(1, ell // 8))
 
 
 @dataclasses.dataclass
@@ -405,6 +408,7 @@ class IterRecord:
     state: tuple | None = None
     reused: bool = False         # the Nystrom factor of the previous iteration was kept
     ref: tuple | None = None     # (ref_p, ref_d) of the PEU at the top of this iteration (record=True)
+    ell: int = 0                 # sketch size of this iteration's factor
 
 
 @dataclasses.dataclass
@@ -428,6 +432,37 @@ class Result:
     zeta: np.ndarray | None = None
     ref_p: float = float("nan")
     ref_d: float = float("nan")
+
+
+# ---------------------------------------------------------------------------
+# Sketch size per IPM iteration (Algorithm 6, "choose sketch size l_k").
+#
+# The paper leaves the choice open and shows its trade-off (the rank-versus-
+# time experiment of the SVM section): a larger sketch makes the factor
+# dearer and the PCG solves cheaper, and the total time has a U-shape in l.
+# READING (builder's rule): with a factor costing about c(l) = cost * l /
+# l_max PCG iterations and PCG work that falls roughly like 1/l, the total is
+# smallest where the two are equal, so after iteration k, with P_k PCG
+# iterations in its two solves, the next sketch doubles when P_k > 2 c(l_k)
+# and halves when P_k < c(l_k) / 2, within [l_min, l_max]; l_0 = l_min.
+# Integer comparisons only, so both implementations take the same decision.
+# Omega_k of size l_k is the first l_k columns of the l_max-wide Omega_k (the
+# test matrices of different iterations stay disjoint draws).
+# ---------------------------------------------------------------------------
+
+def sketch_size_bounds(ell_max: int, ell_min: int) -> int:
+    """The smallest adaptive sketch size: ell_min when given, else l_max / 8."""
+    lo = ell_min if ell_min > 0 else ell_max // 8
+    return max(1, min(lo, ell_max))
+
+
+def sketch_size_next(ell: int, pcg_total: int, ell_min: int, ell_max: int, cost: int) -> int:
+    """The next sketch size from this iteration's PCG count (see above)."""
+    if pcg_total * ell_max > 2 * cost * ell and ell < ell_max:
+        return min(ell_max, 2 * ell)
+    if 2 * pcg_total * ell_max < cost * ell and ell > ell_min:
+        return max(ell_min, (ell + 1) // 2)
+    return ell
 
 
 # ---------------------------------------------------------------------------
@@ -568,7 +603,12 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
     pmm = PMM(lam=lam_pmm, zeta=zeta, rho=rho, delta=delta,
               ref_p=rel_p0 if ref_p0 is None else float(ref_p0),
               ref_d=rel_d0 if ref_d0 is None else float(ref_d0))
-    ell = min(opt.ell, m)
+    ell_max = min(opt.ell, m)
+    adaptive = opt.adapt_cost > 0
+    if adaptive and opt.reuse_pcg > 0:
+        raise ValueError("adaptive sketch size and preconditioner reuse are exclusive")
+    ell_lo = sketch_size_bounds(ell_max, opt.ell_min)
+    ell = ell_lo if adaptive else ell_max
     trace, pcg_counts = [], []
     status = "max_iter"
     forced = list(opt.forced_pcg) if opt.forced_pcg is not None else None
@@ -596,8 +636,10 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         # always with R = 0, Algorithm 6 as written) N_k is sketched afresh.
         reuse = (opt.reuse_pcg > 0 and k > 0 and pcg_counts[-2] <= opt.reuse_pcg
                  and pcg_counts[-1] <= opt.reuse_pcg)
+        if adaptive and k > 0:
+            ell = sketch_size_next(ell, pcg_counts[-2] + pcg_counts[-1], ell_lo, ell_max, opt.adapt_cost)
         if not reuse:
-            Omega = gaussian_omega(opt.seed, k0 + k, m, ell)
+            Omega = gaussian_omega(opt.seed, k0 + k, m, ell_max)[:, :ell]
             F = nystrom(A, D, Omega)
         eta = pcg_tolerance(mu)
         # Predictor (Algorithm 5, first step; Eq. predictor-RHS).
@@ -649,7 +691,7 @@ def solve(A, b, c, q, x0, y0, z0, opt: Options, lam0=None, zeta0=None, k0: int =
         rec = IterRecord(k=k0 + k, mu=mu, rel_p=rel_p, rel_d=rel_d, rho=rho, delta=delta, nu=F.nu,
                          lam_max=float(F.lam[0]), lam_min=float(F.lam[-1]),
                          alpha_p=alpha_p, alpha_d=alpha_d,
-                         pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters, reused=reuse)
+                         pcg_pred=pred.pcg_iters, pcg_corr=corr.pcg_iters, reused=reuse, ell=ell)
         if record:
             rec.state = (x_top, y_top, z_top, state_lam, state_zeta)
             if box:
