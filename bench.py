@@ -37,6 +37,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the batching form runs one stream per problem in flight: let up to 32 of
+# them reach the GPU through separate hardware queues (the default is 8);
+# read when the CUDA context is created, so set before torch is imported
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 

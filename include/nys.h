@@ -51,7 +51,7 @@ typedef enum { NYS_F64 = 0, NYS_F32 = 1, NYS_BF16 = 2, NYS_FP8E4M3 = 3 } nys_dty
 /* Solver options.  Defaults (nys_default_options): tol 1e-6, ell 20,
  * max_ipm_iter 200, max_pcg_iter 1000, seed 0, rho0 = delta0 = 8 (Algorithm 6,
  * second step), reg_floor 5e-10 (the floor seen in Tables 7-8), no forced
- * counts, start_mode 0, reuse_pcg 0. */
+ * counts, start_mode 0, reuse_pcg 0, adapt_cost 0, ell_min 0. */
 typedef struct {
     double tol;                   /* relative KKT tolerance of the termination test  */
     int ell;                      /* Nystrom sketch size (clamped to m)               */
@@ -87,6 +87,18 @@ typedef struct {
      * the current delta) while both PCG solves of the previous iteration took
      * at most R iterations. */
     int reuse_pcg;
+    /* Sketch size per IPM iteration (Algorithm 6, "choose sketch size l_k"):
+     * 0 = every factor has the problem's ell (l_max).  C > 0 = adaptive: with
+     * a factor taken to cost about C * l / l_max PCG iterations, iteration k
+     * is followed by a doubled sketch when its two PCG solves took more than
+     * 2 C l_k / l_max iterations and by a halved one when they took fewer than
+     * C l_k / (2 l_max), within [ell_min, l_max]; the first factor uses
+     * ell_min (0 = max(1, l_max / 8)).  Omega_k of size l_k is the first l_k
+     * columns of the l_max-wide Omega_k.  Not combined with reuse_pcg or with
+     * nys_solve_batched (NYS_ERR_ARG); a resumed solve starts again at
+     * ell_min. */
+    int adapt_cost;
+    int ell_min;
 } nys_options;
 
 /* One QP.  With host == 0 all pointers are device pointers; with host == 1
@@ -179,6 +191,9 @@ typedef struct {
     int sketches;                 /* Nystrom factors built (= ipm_iters unless reused) */
     double peu_ref_p, peu_ref_d;  /* final references of the PMM update (resumable    */
                                   /*   state together with lam, zeta, rho, delta)      */
+    int* ell_log;                 /* optional host array: sketch size of each factor  */
+    int ell_log_cap;              /*   built, in order (capacity in entries)           */
+    int ell_log_len;              /* entries written                                   */
 } nys_result;
 
 /* Fill *opt with the defaults listed above. */

@@ -789,6 +789,15 @@ cudaError_t launch_trsm(cudaStream_t st, int m, int ell, double* B, int ld, cons
 
 }  // namespace
 
+bool nystrom_core_capturable(int m, int ell) {
+  // the direct route (no Cholesky QR copies) with the cluster or one-CTA Jacobi
+  const bool direct = (ell <= kJacobiClusterMaxEll && ell >= 2 && m <= kJacobiClusterMaxRows) ||
+                      (m <= 2 * ell && (long long)m * ell <= kJacobiSmemElems);
+  if (!direct) return false;
+  return (ell <= kJacobiClusterMaxEll && ell >= 2 && m <= kJacobiClusterMaxRows) ||
+         (long long)m * ell <= kJacobiSmemElems;
+}
+
 cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, const double* Om,
                              int ld, double* U, double* lam, double* sd, int* si, RedBuf red,
                              CoreWork cw, int num_sms) {

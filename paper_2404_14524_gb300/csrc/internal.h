@@ -69,8 +69,10 @@ cudaError_t scaling_f64(cudaStream_t st, int n, const double* x, const double* z
                         double rho, double* D);
 
 // ---------------------------------------------------------------- sketch
+// Omega_k of width ell (the counter stride); only its first `cols` columns
+// are written (cols < 0: all ell).
 cudaError_t gaussian_omega(cudaStream_t st, unsigned long long seed, int k, int m, int ell,
-                           double* Om, int ld);
+                           double* Om, int ld, int cols = -1);
 // C(r, c) = sum_k Aop(r, k) * Bop(k, c) * (scale ? scale[k] : 1), FP64.
 // Aop(r, k) = A[r * sar + k * sak], Bop(k, c) = B[k * sbk + c * sbc], C[r * scr + c * scc].
 // One of sar/sak must be 1, and sbk must be 1.
@@ -220,6 +222,7 @@ struct ClusterPcgTask {
   int* iters;                           // device: iterations taken
   double* sd;                           // device scalars: SD_RR, SD_BNORM2, SD_ETA2 written
   int* err;                             // device error word
+  unsigned long long* t_ns;             // device, optional: the launch's duration is added (ns)
 };
 struct ClusterPlan {
   int C = 0;                            // CTAs per cluster (4, 8 or 16)
@@ -234,6 +237,47 @@ bool pcg_cluster_plan(int m, int n, int ell, int policy, ClusterPlan* plan);
 // array `tasks`, each planned no larger than `plan`.
 cudaError_t pcg_cluster_f64(cudaStream_t st, const ClusterPlan& plan, const ClusterPcgTask& task,
                             const ClusterPcgTask* tasks, int count);
+// ---------------------------------------------------------------- device-resident IPM iteration
+// Scalars of one IP-PMM run kept in device memory (see ipm_dev.cu).
+struct IpmDev {
+  double mu, mu_prev, rho, delta, ref_p, ref_d, rel_p, rel_d, eta;
+  double ap, ad, ap_bar, ad_bar, mu_t;
+  double tol, floor, pden, dden, nmu;   // tolerance, PMM floor, 1 + ||b||, 1 + ||c||, n
+  int k, k0, done, status, warn;
+  int forced_ipm, max_ipm, n_forced, max_pcg;
+  int solves, pcg_total, recentre_p, recentre_d;
+  unsigned long long pcg_ns;            // device time of the PCG launches
+};
+cudaError_t ipm_residuals_dev(cudaStream_t st, int m, int n, const double* b, const double* c, const double* q,
+                              const double* x, const double* y, const double* z, const double* Ax,
+                              const double* Aty, const double* lam, const double* zeta, const IpmDev* s,
+                              double* r_d, double* r_p, double* r_xz, double* red_out, RedBuf red);
+cudaError_t scaling_dev(cudaStream_t st, int n, const double* x, const double* z, const double* q, const IpmDev* s,
+                        double* D);
+cudaError_t mu_aff_dev(cudaStream_t st, int n, const double* x, const double* dx, const double* z, const double* dz,
+                       const IpmDev* s, double* out, RedBuf red);
+cudaError_t corrector_rhs_dev(cudaStream_t st, int n, const IpmDev* s, const double* dxp, const double* dzp,
+                              double* r_xz);
+cudaError_t ipm_update_dev(cudaStream_t st, int m, int n, const IpmDev* s, const double* dx, const double* dy,
+                           const double* dz, double* x, double* y, double* z);
+cudaError_t ipm_recentre(cudaStream_t st, int m, int n, const IpmDev* s, const double* y, const double* x,
+                         double* lam, double* zeta);
+cudaError_t ipm_top_dev(cudaStream_t st, IpmDev* s, const double* red_out, ClusterPcgTask* tasks, const int* forced,
+                        int* err);
+cudaError_t ipm_after_pcg_dev(cudaStream_t st, IpmDev* s, const ClusterPcgTask* task, const int* si, const double* sd,
+                              int* log, int log_cap);
+cudaError_t ipm_steps_dev(cudaStream_t st, IpmDev* s, const double* red_out, int final_step);
+cudaError_t ipm_mu_t_dev(cudaStream_t st, IpmDev* s, const double* red_out);
+cudaError_t ipm_iter_end_dev(cudaStream_t st, IpmDev* s);
+cudaError_t ipm_cond_dev(cudaStream_t st, cudaGraphConditionalHandle cond, const IpmDev* s);
+// Omega_k with k = *k_dev + k0 read on the device (width ell, as gaussian_omega)
+cudaError_t gaussian_omega_dev(cudaStream_t st, unsigned long long seed, const int* k_dev, int k0, int m, int ell,
+                               double* Om, int ld);
+// Whether the Nystrom core of an m x ell sketch runs as plain and cluster
+// kernel launches only (no cooperative launch, no copy): capturable in a
+// conditional graph body.
+bool nystrom_core_capturable(int m, int ell);
+
 // Body-graph tail of a conditional while node: keep looping while !SI_DONE.
 cudaError_t pcg_loop_condition(cudaStream_t st, cudaGraphConditionalHandle cond, const int* si);
 

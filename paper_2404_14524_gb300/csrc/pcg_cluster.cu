@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(kCT, kAS ? 1 : 3) k_pcg_cluster(ClusterPcgTask
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const ClusterPcgTask T = tasks ? tasks[blockIdx.x / C] : t0;
+  unsigned long long t_start = 0;
+  if (T.t_ns && rank == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
   extern __shared__ double smem[];
   __shared__ double sh[kCW];
   const int m = T.m, n = T.n, ell = T.ell;
@@ -475,6 +477,11 @@ __global__ void __launch_bounds__(kCT, kAS ? 1 : 3) k_pcg_cluster(ClusterPcgTask
     T.sd[SD_RR] = rr;
     T.sd[SD_BNORM2] = bnorm2;
     T.sd[SD_ETA2] = T.eta2;
+    if (T.t_ns) {
+      unsigned long long t_end;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+      atomicAdd(T.t_ns, t_end - t_start);
+    }
   }
   cl.sync();   // no CTA leaves while a peer may still read its shared memory
 }

@@ -22,13 +22,29 @@ __device__ __forceinline__ unsigned long long splitmix_at(unsigned long long see
   return z ^ (z >> 31);
 }
 
-__global__ void k_gaussian(unsigned long long seed, int k, int m, int ell, double* __restrict__ Om,
+__global__ void k_gaussian(unsigned long long seed, int k, int m, int ell, int cols, double* __restrict__ Om,
                            int ld) {
+  const long long idx = (long long)blockIdx.x * kNT + threadIdx.x;
+  if (idx >= (long long)m * cols) return;
+  const int i = (int)(idx % m);
+  const int j = (int)(idx / m);
+  const unsigned long long c = ((unsigned long long)k * ell + j) * (unsigned long long)m + i;
+  const unsigned long long b1 = splitmix_at(seed, 2ull * c);
+  const unsigned long long b2 = splitmix_at(seed, 2ull * c + 1ull);
+  const double u1 = ((double)(b1 >> 11) + 0.5) * 0x1.0p-53;
+  const double u2 = ((double)(b2 >> 11) + 0.5) * 0x1.0p-53;
+  const double two_pi = 2.0 * 3.141592653589793;
+  Om[(size_t)j * ld + i] = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+}
+
+__global__ void k_gaussian_dev(unsigned long long seed, const int* __restrict__ k_dev, int k0, int m, int ell,
+                               double* __restrict__ Om, int ld) {
   const long long idx = (long long)blockIdx.x * kNT + threadIdx.x;
   if (idx >= (long long)m * ell) return;
   const int i = (int)(idx % m);
   const int j = (int)(idx / m);
-  const unsigned long long c = ((unsigned long long)k * ell + j) * (unsigned long long)m + i;
+  const unsigned long long k = (unsigned long long)(*k_dev + k0);
+  const unsigned long long c = (k * ell + j) * (unsigned long long)m + i;
   const unsigned long long b1 = splitmix_at(seed, 2ull * c);
   const unsigned long long b2 = splitmix_at(seed, 2ull * c + 1ull);
   const double u1 = ((double)(b1 >> 11) + 0.5) * 0x1.0p-53;
@@ -130,11 +146,21 @@ __global__ void k_splitk_reduce(int M, int N, int S, const double* __restrict__ 
 }  // namespace
 
 cudaError_t gaussian_omega(cudaStream_t st, unsigned long long seed, int k, int m, int ell,
-                           double* Om, int ld) {
+                           double* Om, int ld, int cols) {
+  if (cols < 0 || cols > ell) cols = ell;
+  const long long total = (long long)m * cols;
+  if (total <= 0) return cudaSuccess;
+  count_launches(1);
+  k_gaussian<<<(unsigned)((total + kNT - 1) / kNT), kNT, 0, st>>>(seed, k, m, ell, cols, Om, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t gaussian_omega_dev(cudaStream_t st, unsigned long long seed, const int* k_dev, int k0, int m, int ell,
+                               double* Om, int ld) {
   const long long total = (long long)m * ell;
   if (total <= 0) return cudaSuccess;
   count_launches(1);
-  k_gaussian<<<(unsigned)((total + kNT - 1) / kNT), kNT, 0, st>>>(seed, k, m, ell, Om, ld);
+  k_gaussian_dev<<<(unsigned)((total + kNT - 1) / kNT), kNT, 0, st>>>(seed, k_dev, k0, m, ell, Om, ld);
   return cudaGetLastError();
 }
 

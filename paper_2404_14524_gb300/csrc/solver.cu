@@ -117,6 +117,29 @@ struct nys_solver {
   size_t lp_part_cap = 0;
   bool lp_bf16_stage = true;   // BF16 corrections still contracting in this solve
   int trace = 0;               // NYS_TRACE=1: one line per IPM iteration on stderr
+  // the Nystrom factor now in U / lamh: built for the FP64 matrix fac_A
+  // (m = fac_m, sketch size fac_ell) by the last IPM iteration of a solve
+  const void* fac_A = nullptr;
+  int fac_m = 0, fac_ell = 0;
+  // device-resident IPM iteration (ipm_dev.cu) for problems (P) in the FP64
+  // form on a cluster PCG route: its scalars, the two PCG tasks of an
+  // iteration, the forced counts and the PCG log live in device memory, and
+  // a whole solve is one graph (kept while the problem's pointers, shapes and
+  // launch plan stay the same)
+  IpmDev* ipmd = nullptr;
+  ClusterPcgTask* dtask = nullptr;     // 2: predictor, corrector
+  int* d_forced = nullptr;
+  int* d_pcglog = nullptr;
+  int dev_log_cap = 0;
+  IpmDev* h_ipmd = nullptr;            // pinned mirror
+  int* h_pcglog = nullptr;             // pinned mirror
+  cudaGraph_t ipm_graph = nullptr;
+  cudaGraphExec_t ipm_exec = nullptr;
+  const void* ik_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // A, b, c, q, plan key
+  long long ik_lda = 0;
+  int ik_m = 0, ik_n = 0, ik_ell = 0, ik_C = 0, ik_as = 0;
+  unsigned ipm_kernels_top = 0, ipm_kernels_body = 0;
+  bool use_dev_ipm = true;             // NYS_DEVICE_IPM=0 keeps the host-driven iteration
   // batching form: worker solvers (created on first use), one per in-flight QP
   int max_batch = 0;
   std::vector<nys_solver*> workers;
@@ -232,6 +255,11 @@ size_t carve(nys_solver* h, char* base) {
   h->dsp = c.take<double>(N);
   h->dwc = c.take<double>(N);
   h->dsc = c.take<double>(N);
+  h->dev_log_cap = 2 * std::max(0, h->opt.max_ipm_iter) + 8;
+  h->ipmd = c.take<IpmDev>(1);
+  h->dtask = c.take<ClusterPcgTask>(2);
+  h->d_forced = c.take<int>(h->dev_log_cap);
+  h->d_pcglog = c.take<int>(h->dev_log_cap);
   return c.off;
 }
 
@@ -302,6 +330,14 @@ int sync_scalars_at(nys_solver* h, int off, int n_red) {
   CK(cudaMemcpyAsync(h->h_red + off, h->red_out + off, sizeof(double) * n_red, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return check_err(h);
+}
+
+void drop_ipm_graph(nys_solver* h) {
+  if (h->ipm_exec) cudaGraphExecDestroy(h->ipm_exec);
+  if (h->ipm_graph) cudaGraphDestroy(h->ipm_graph);
+  h->ipm_exec = nullptr;
+  h->ipm_graph = nullptr;
+  h->ik_ptr[0] = nullptr;
 }
 
 void drop_pcg_graph(nys_solver* h) {
@@ -593,9 +629,9 @@ int op_Aty(nys_solver* h, const Prob& P, const double* y, const double* scale, d
 }
 
 // Y = A (D .* (A^T Omega_k)) into h->Y, Omega_k into h->Om (FP64 panels).
-int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D) {
+int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D, int ell_stride = 0) {
   const nys_options& o = h->opt;
-  CK(gaussian_omega(h->st, o.seed, k, P.m, ell, h->Om, h->ld));
+  CK(gaussian_omega(h->st, o.seed, k, P.m, ell_stride > 0 ? ell_stride : ell, h->Om, h->ld, ell));
   if (!P.lp) {
     CK(sketch_f64(h->st, P.m, P.n, P.A64, P.lda, D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf,
                   h->split_cap));
@@ -742,6 +778,7 @@ struct IpmRun {
   nys_result* r = nullptr;
   std::chrono::steady_clock::time_point t0, tk0;
   int m = 0, n = 0, lp = 0, ell = 0;
+  int ell_max = 0, ell_lo = 0;  // adaptive sketch size: bounds (ell = the current l_k)
   long long lda = 0;
   Prob P{};
   const double* A = nullptr;
@@ -817,6 +854,15 @@ struct IpmRun {
   int mid();
   int bottom();
   int finish();
+  // the device-resident iteration (problems (P), FP64 form, cluster PCG)
+  bool device_eligible();
+  int dev_top();
+  int dev_body();
+  int device_prepare();
+  int device_step();
+  int device_collect();
+  int device_solve();
+  cudaGraphExec_t dev_exec = nullptr;
 };
 
 int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
@@ -836,12 +882,20 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
                          "nys_solve: bad problem (sizes, dtype for the precision mode, or null pointers)");
   }
   ell = std::min(std::min(h->ell_cap, m), p->ell > 0 ? p->ell : h->ell_cap);
+  ell_max = ell;
+  ell_lo = std::max(1, std::min(o.ell_min > 0 ? o.ell_min : ell_max / 8, ell_max));
+  if (o.adapt_cost < 0 || o.ell_min < 0 || (o.adapt_cost > 0 && o.reuse_pcg > 0)) {
+    done = true;
+    return status = fail(h, NYS_ERR_ARG, "nys_solve: adapt_cost / ell_min negative, or adapt_cost with reuse_pcg");
+  }
   lda = p->lda;
   r->status = NYS_OK;
   r->ipm_iters = 0;
   r->pcg_iters_total = 0;
   r->refine_steps = 0;
   r->pcg_log_len = 0;
+  r->ell_log_len = 0;
+  h->fac_A = nullptr;          // U / lamh are about to be overwritten
   r->pcg_seconds = 0.0;
   r->sketches = 0;
   h->pcg_ms = 0.0;
@@ -934,6 +988,7 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   delta = o.delta0;
   ref_p = p->has_peu_ref ? p->peu_ref_p : -1.0;
   ref_d = p->has_peu_ref ? p->peu_ref_d : -1.0;
+  if (o.adapt_cost > 0) ell = ell_lo;   // the practical start above used l_max
   status = NYS_WARN_MAXITER;
   done = false;
   return NYS_OK;
@@ -1105,12 +1160,23 @@ int IpmRun::top() {
   if (box) CK(box_scaling_f64(h->st, n, h->vk, h->x, h->z, h->w, h->s, q, rho, h->D));
   else CK(scaling_f64(h->st, n, h->x, h->z, q, rho, h->D));
   reused = o.reuse_pcg > 0 && k > 0 && last_pred <= o.reuse_pcg && last_corr <= o.reuse_pcg;
+  if (o.adapt_cost > 0 && k > 0) {
+    // sketch size of this iteration from the previous one's PCG count
+    // (integer tests, the same decisions as the oracle's)
+    const long long pc = (long long)last_pred + last_corr, C = o.adapt_cost;
+    if (pc * ell_max > 2 * C * ell && ell < ell_max) ell = std::min(ell_max, 2 * ell);
+    else if (2 * pc * ell_max < C * ell && ell > ell_lo) ell = std::max(ell_lo, (ell + 1) / 2);
+  }
   if (!reused) {
-    rc = op_sketch(h, P, p->k0 + k, ell, h->D);
+    if (r->ell_log && r->ell_log_len < r->ell_log_cap) r->ell_log[r->ell_log_len++] = ell;
+    rc = op_sketch(h, P, p->k0 + k, ell, h->D, ell_max);
     if (rc != NYS_OK) { stop(rc); return rc; }
     CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red,
                         h->cw, h->num_sms));
     ++r->sketches;
+    h->fac_A = lp ? nullptr : A;
+    h->fac_m = m;
+    h->fac_ell = ell;
   }
   eta = std::max(1e-10, std::min(1e-2, 0.1 * mu));
   t_pre = 0.0;
@@ -1229,6 +1295,214 @@ int IpmRun::bottom() {
   return NYS_OK;
 }
 
+// ---------------------------------------------------------------- device-resident iteration
+// Problems (P) in the FP64 form whose PCG runs on a thread-block cluster and
+// whose Nystrom core is plain kernel launches take this path: the decisions
+// of top(), mid() and bottom() are made by the one-thread kernels of
+// ipm_dev.cu, and one IPM iteration (its Newton steps and the next
+// iteration's top) is one CUDA graph launch with one read-back of the device
+// scalars.  The kernels, their order and their arithmetic are those of the
+// host-driven phases.
+bool IpmRun::device_eligible() {
+  const nys_options& o = h->opt;
+  if (!h->use_dev_ipm || !h->use_graphs || lp || box || h->trace || o.reuse_pcg > 0 || o.adapt_cost > 0) return false;
+  if (2 * std::max(0, o.max_ipm_iter) + 8 > h->dev_log_cap) return false;
+  const int nf = p->forced_override ? p->n_forced_pcg : o.n_forced_pcg;
+  if (nf > h->dev_log_cap) return false;
+  const int route = fp64_route(h, m, n, ell);
+  if (route != NYS_ROUTE_CLUSTER_SMEM && route != NYS_ROUTE_CLUSTER_L2) return false;
+  return nystrom_core_capturable(m, ell);
+}
+
+// Top of an iteration: A x, A^T y, residual sums, the scalar decisions, the
+// re-centred estimates and the predictor's right-hand sides.
+int IpmRun::dev_top() {
+  int rc = op_Ax(h, P, h->x, 0.0, nullptr, h->Ax);
+  if (rc == NYS_OK) rc = op_Aty(h, P, h->y, nullptr, h->Aty);
+  if (rc != NYS_OK) return rc;
+  CK(ipm_residuals_dev(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta, h->ipmd, h->r_d,
+                       h->r_p, h->r_xz, h->red_out, h->red));
+  CK(ipm_top_dev(h->st, h->ipmd, h->red_out, h->dtask, h->d_forced, h->si + SI_ERR));
+  CK(ipm_recentre(h->st, m, n, h->ipmd, h->y, h->x, h->lam, h->zeta));
+  CK(ipm_residuals_dev(h->st, m, n, b, c, q, h->x, h->y, h->z, h->Ax, h->Aty, h->lam, h->zeta, h->ipmd, h->r_d,
+                       h->r_p, h->r_xz, h->red_out, h->red));
+  return NYS_OK;
+}
+
+// Iteration k (Algorithm 6 with Algorithm 5) and the top of iteration k+1.
+int IpmRun::dev_body() {
+  const nys_options& o = h->opt;
+  const int cap = h->dev_log_cap;
+  CK(scaling_dev(h->st, n, h->x, h->z, q, h->ipmd, h->D));
+  CK(gaussian_omega_dev(h->st, o.seed, &h->ipmd->k, p->k0, m, ell, h->Om, h->ld));
+  CK(sketch_f64(h->st, m, n, A, lda, h->D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf, h->split_cap));
+  CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red, h->cw,
+                      h->num_sms));
+  // predictor
+  int rc = newton_begin(h, m, n, A, lda, h->x, h->D, h->r_d, h->r_p, h->r_xz);
+  if (rc != NYS_OK) return rc;
+  CK(pcg_cluster_f64(h->st, h->cp, ClusterPcgTask{}, h->dtask, 1));
+  CK(ipm_after_pcg_dev(h->st, h->ipmd, h->dtask, h->si, h->sd, h->d_pcglog, cap));
+  rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, h->r_d, h->r_xz, h->dyp, h->dxp, h->dzp);
+  if (rc != NYS_OK) return rc;
+  CK(step_ratios_f64(h->st, n, h->x, h->dxp, h->z, h->dzp, h->red_out, h->red));
+  CK(ipm_steps_dev(h->st, h->ipmd, h->red_out, 0));
+  CK(mu_aff_dev(h->st, n, h->x, h->dxp, h->z, h->dzp, h->ipmd, h->red_out, h->red));
+  CK(ipm_mu_t_dev(h->st, h->ipmd, h->red_out));
+  CK(corrector_rhs_dev(h->st, n, h->ipmd, h->dxp, h->dzp, h->r_xz));
+  // corrector
+  rc = newton_begin(h, m, n, A, lda, h->x, h->D, nullptr, nullptr, h->r_xz);
+  if (rc != NYS_OK) return rc;
+  CK(pcg_cluster_f64(h->st, h->cp, ClusterPcgTask{}, h->dtask + 1, 1));
+  CK(ipm_after_pcg_dev(h->st, h->ipmd, h->dtask + 1, h->si, h->sd, h->d_pcglog, cap));
+  rc = newton_end(h, m, n, A, lda, h->x, h->z, h->D, nullptr, h->r_xz, h->dyc, h->dxc, h->dzc);
+  if (rc != NYS_OK) return rc;
+  CK(add_dirs_f64(h->st, m, n, h->dxp, h->dyp, h->dzp, h->dxc, h->dyc, h->dzc));
+  CK(step_ratios_f64(h->st, n, h->x, h->dxc, h->z, h->dzc, h->red_out, h->red));
+  CK(ipm_steps_dev(h->st, h->ipmd, h->red_out, 1));
+  CK(ipm_update_dev(h->st, m, n, h->ipmd, h->dxc, h->dyc, h->dzc, h->x, h->y, h->z));
+  CK(ipm_iter_end_dev(h->st, h->ipmd));
+  return dev_top();
+}
+
+// Device scalars and PCG tasks of this run, the top of iteration 0, and the
+// iteration graph (captured once per problem and launch plan).
+int IpmRun::device_prepare() {
+  const nys_options& o = h->opt;
+  IpmDev& hd = *h->h_ipmd;
+  std::memset(&hd, 0, sizeof(hd));
+  hd.rho = rho;
+  hd.delta = delta;
+  hd.ref_p = ref_p;
+  hd.ref_d = ref_d;
+  hd.tol = o.tol;
+  hd.floor = o.reg_floor;
+  hd.pden = 1.0 + pnorm;
+  hd.dden = 1.0 + cnorm;
+  hd.nmu = (double)n;
+  hd.k0 = p->k0;
+  hd.forced_ipm = forced_ipm();
+  hd.max_ipm = o.max_ipm_iter;
+  hd.max_pcg = o.max_pcg_iter;
+  const int* f = p->forced_override ? p->forced_pcg_iters : o.forced_pcg_iters;
+  const int nf = f ? (p->forced_override ? p->n_forced_pcg : o.n_forced_pcg) : 0;
+  hd.n_forced = nf;
+  if (nf > 0) CK(cudaMemcpyAsync(h->d_forced, f, sizeof(int) * nf, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->ipmd, &hd, sizeof(IpmDev), cudaMemcpyHostToDevice, h->st));
+  ClusterPcgTask t[2] = {};
+  for (int w = 0; w < 2; ++w) {
+    t[w].m = m; t[w].n = n; t[w].ell = ell; t[w].ld = h->ld; t[w].lda = lda;
+    t[w].A = A; t[w].D = h->D; t[w].U = h->U; t[w].lam = h->lamh; t[w].xi = h->xi;
+    t[w].x = w == 0 ? h->dyp : h->dyc;
+    t[w].iters = h->si + SI_ITERS; t[w].sd = h->sd; t[w].err = h->si + SI_ERR;
+    t[w].t_ns = &h->ipmd->pcg_ns;
+    t[w].max_iter = o.max_pcg_iter;
+  }
+  CK(cudaMemcpyAsync(h->dtask, t, sizeof(t), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
+  int rc = dev_top();
+  if (rc != NYS_OK) return rc;
+  // the iteration graph
+  const void* key[5] = {A, b, c, q, reinterpret_cast<const void*>(h->U)};
+  bool same = h->ipm_exec && h->ik_lda == lda && h->ik_m == m && h->ik_n == n && h->ik_ell == ell &&
+              h->ik_C == h->cp.C && h->ik_as == h->cp.a_smem;
+  for (int i = 0; i < 5 && same; ++i) same = h->ik_ptr[i] == key[i];
+  if (!same) {
+    drop_ipm_graph(h);
+    cudaStream_t saved = h->st;
+    h->st = h->cap_stream;
+    const unsigned long long c0 = g_launches.load();
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int brc = e == cudaSuccess ? dev_body() : NYS_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &g) : e;
+    h->st = saved;
+    const unsigned per = (unsigned)(g_launches.load() - c0);
+    g_launches.fetch_sub(per);            // counted when the graph runs
+    cudaGraphExec_t ex = nullptr;
+    if (brc != NYS_OK || e2 != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      h->use_dev_ipm = false;             // this handle keeps the host-driven iteration
+      return 1;
+    }
+    h->ipm_graph = g;
+    h->ipm_exec = ex;
+    h->ipm_kernels_body = per;
+    for (int i = 0; i < 5; ++i) h->ik_ptr[i] = key[i];
+    h->ik_lda = lda; h->ik_m = m; h->ik_n = n; h->ik_ell = ell; h->ik_C = h->cp.C; h->ik_as = h->cp.a_smem;
+  }
+  dev_exec = h->ipm_exec;
+  CK(cudaMemcpyAsync(h->h_ipmd, h->ipmd, sizeof(IpmDev), cudaMemcpyDeviceToHost, h->st));
+  return NYS_OK;
+}
+
+// After the previous read-back completed: launch the next iteration when the
+// run is not done (returns 1 while iterations remain in flight, 0 when done).
+int IpmRun::device_step() {
+  if (h->h_ipmd->done) return 0;
+  CK(cudaGraphLaunch(dev_exec, h->st));
+  count_launches(h->ipm_kernels_body);
+  CK(cudaMemcpyAsync(h->h_ipmd, h->ipmd, sizeof(IpmDev), cudaMemcpyDeviceToHost, h->st));
+  return 1;
+}
+
+// Results of a finished device-resident run (stream synchronised).
+int IpmRun::device_collect() {
+  const IpmDev& hd = *h->h_ipmd;
+  const int nlog = std::min(hd.solves, h->dev_log_cap);
+  if (nlog > 0) {
+    CK(cudaMemcpyAsync(h->h_pcglog, h->d_pcglog, sizeof(int) * nlog, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  for (int i = 0; i < nlog; ++i) log_pcg(h->h_pcglog[i]);
+  k = hd.k;
+  mu = hd.mu;
+  mu_prev = hd.mu_prev;
+  rel_p = hd.rel_p;
+  rel_d = hd.rel_d;
+  rho = hd.rho;
+  delta = hd.delta;
+  ref_p = hd.ref_p;
+  ref_d = hd.ref_d;
+  eta = hd.eta;
+  if (hd.warn) warn = hd.warn;
+  r->sketches += hd.k;
+  h->pcg_ms += 1e-6 * (double)hd.pcg_ns;
+  if (hd.k > 0) {
+    h->fac_A = A;
+    h->fac_m = m;
+    h->fac_ell = ell;
+  }
+  int code = hd.done ? hd.status : NYS_ERR_CUDA;
+  if (code < 0) {
+    if (h->h_si) {
+      CK(cudaMemcpyAsync(h->h_si, h->si, sizeof(int) * SI_COUNT, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
+    const int e = check_err(h);
+    code = fail(h, e != NYS_OK ? e : code, "device-resident IPM iteration stopped with status %d at k=%d",
+                hd.status, hd.k);
+  }
+  stop(code);
+  return NYS_OK;
+}
+
+// A whole solve on the device-resident path: 0 when it ran, 1 when this
+// run must use the host-driven phases, < 0 on a CUDA failure.
+int IpmRun::device_solve() {
+  int rc = device_prepare();
+  if (rc != NYS_OK) return rc;
+  CK(cudaStreamSynchronize(h->st));
+  while (true) {
+    rc = device_step();
+    if (rc < 0) return rc;
+    if (rc == 0) break;
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return device_collect();
+}
+
 // Outputs and final measures.
 int IpmRun::finish() {
   const cudaMemcpyKind kout = p->host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -1256,6 +1530,7 @@ int IpmRun::finish() {
   if (status == NYS_OK && warn != NYS_OK) status = warn;
   if (status >= 0 && rc2 != NYS_OK) status = rc2;
   if (status >= 0 && h->h_red[7] != 0.0) status = fail(h, NYS_ERR_NUMERIC, "non-finite final iterate");
+  if (status < 0) h->fac_A = nullptr;   // no factor to offer the adjoint
   r->status = status;
   r->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   r->pcg_seconds = h->pcg_ms * 1e-3;
@@ -1437,6 +1712,8 @@ void nys_default_options(nys_options* o) {
   o->forced_ipm_iters = -1;
   o->start_mode = 0;
   o->reuse_pcg = 0;
+  o->adapt_cost = 0;
+  o->ell_min = 0;
 }
 
 const char* nys_last_error(nys_handle h) { return h ? h->err.c_str() : "null handle"; }
@@ -1473,7 +1750,9 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   }
   carve(h, static_cast<char*>(h->arena));
   if (cudaMallocHost(&h->h_red, sizeof(double) * 64) != cudaSuccess ||
-      cudaMallocHost(&h->h_si, sizeof(int) * 64) != cudaSuccess) {
+      cudaMallocHost(&h->h_si, sizeof(int) * 64) != cudaSuccess ||
+      cudaMallocHost(&h->h_ipmd, sizeof(IpmDev)) != cudaSuccess ||
+      cudaMallocHost(&h->h_pcglog, sizeof(int) * h->dev_log_cap) != cudaSuccess) {
     cudaFree(h->arena);
     delete h;
     return NYS_ERR_NOMEM;
@@ -1505,6 +1784,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   }
   if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
   if (const char* env = std::getenv("NYS_JACOBI_F32")) h->cw.f32_start = (env[0] != '0');
+  if (const char* env = std::getenv("NYS_DEVICE_IPM")) h->use_dev_ipm = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess) {
     cudaFree(h->arena);
@@ -1524,6 +1804,7 @@ int nys_destroy(nys_handle h) {
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   drop_pcg_graph(h);
+  drop_ipm_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ev_pcg0) cudaEventDestroy(h->ev_pcg0);
   if (h->ev_pcg1) cudaEventDestroy(h->ev_pcg1);
@@ -1537,6 +1818,8 @@ int nys_destroy(nys_handle h) {
   if (h->stage) cudaFree(h->stage);
   cudaFreeHost(h->h_red);
   cudaFreeHost(h->h_si);
+  if (h->h_ipmd) cudaFreeHost(h->h_ipmd);
+  if (h->h_pcglog) cudaFreeHost(h->h_pcglog);
   delete h;
   return NYS_OK;
 }
@@ -1714,10 +1997,98 @@ int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long
                 ld, lam, eta, max_iter, forced_iters, dx, dy, dz, iters);
 }
 
+namespace {
+
+// One run on the host-driven phases (the fallback of batch_device).
+void host_run(IpmRun& run) {
+  while (!run.done) {
+    if (run.top() < 0 && !run.done) run.stop(NYS_ERR_CUDA);
+    if (run.done) break;
+    if (run.req.active) serve_single(run);
+    if (run.mid() < 0 && !run.done) run.stop(NYS_ERR_CUDA);
+    if (run.done) break;
+    if (run.req.active) serve_single(run);
+    if (run.bottom() < 0 && !run.done) run.stop(NYS_ERR_CUDA);
+  }
+  run.finish();
+}
+
+// Batching form on the device-resident iteration.  Each worker solver holds
+// one problem at a time; its iterations are graph launches on the worker's
+// stream, each followed by a read-back of the device scalars.  One host
+// thread polls the worker streams and launches the next iteration of
+// whichever problem's read-back has arrived, so every problem advances at
+// its own pace (no lock step: a short solve does not wait for a long one),
+// and a worker takes the next problem as soon as its current one finishes.
+// Problems the path does not take run on the host-driven phases.
+int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, const std::vector<int>& order,
+                 int want) {
+  std::vector<IpmRun> runs(want);
+  std::vector<int> busy(want, 0);
+  int next = 0, active = 0;
+  auto begin = [&](int t) -> bool {
+    while (next < count) {
+      const int pi = order[next++];
+      IpmRun& run = runs[t];
+      run = IpmRun();
+      if (run.start(h->workers[t], &p[pi], &r[pi]) != NYS_OK) {
+        r[pi].status = run.status;
+        continue;
+      }
+      if (!run.device_eligible()) {
+        host_run(run);
+        continue;
+      }
+      const int rc = run.device_prepare();
+      if (rc == 1) {                      // the graph could not be captured: host path
+        host_run(run);
+        continue;
+      }
+      if (rc < 0) {
+        run.stop(rc);
+        run.finish();
+        continue;
+      }
+      return true;
+    }
+    return false;
+  };
+  for (int t = 0; t < want; ++t)
+    if (begin(t)) { busy[t] = 1; ++active; }
+  while (active > 0) {
+    bool progressed = false;
+    for (int t = 0; t < want; ++t) {
+      if (!busy[t]) continue;
+      const cudaError_t q = cudaStreamQuery(h->worker_streams[t]);
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      IpmRun& run = runs[t];
+      int rc = q == cudaSuccess ? run.device_step() : NYS_ERR_CUDA;
+      if (rc == 1) continue;              // the next iteration is in flight
+      if (rc < 0) {
+        cudaGetLastError();
+        run.stop(fail(h, NYS_ERR_CUDA, "nys_solve_batched: worker %d stream failed", t));
+      } else {
+        run.device_collect();
+      }
+      run.finish();
+      busy[t] = 0;
+      --active;
+      if (begin(t)) { busy[t] = 1; ++active; }
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  return NYS_OK;
+}
+
+}  // namespace
+
 int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result* r) {
   if (!h) return NYS_ERR_ARG;
   if (count < 0 || (count > 0 && (!p || !r))) return fail(h, NYS_ERR_ARG, "nys_solve_batched: bad argument");
   if (h->max_batch < 1) return fail(h, NYS_ERR_ARG, "nys_solve_batched: handle created with max_batch = 0");
+  if (h->opt.adapt_cost > 0)
+    return fail(h, NYS_ERR_ARG, "nys_solve_batched: the adaptive sketch size is for single solves");
   if (count == 0) return NYS_OK;
   const int want = std::min(h->max_batch, count);
   // the caller's stream must be drained before worker streams read its data
@@ -1732,6 +2103,11 @@ int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result*
       cudaStreamDestroy(s);
       return fail(h, rc, "nys_solve_batched: cannot create worker solver %zu", h->workers.size());
     }
+    // many systems side by side: a cluster plan reading A from L2 when A does
+    // not fit on chip (the shared launches use the same plans)
+    if (w->pcg_path == 0) w->plan_policy = 2;
+    if (const char* env = std::getenv("NYS_BATCH_PLAN"))   // 1: throughput plans (4-8 CTAs) only
+      if (env[0] == '1' && w->pcg_path == 0) w->plan_policy = 1;
     h->workers.push_back(w);
     h->worker_streams.push_back(s);
   }
@@ -1753,6 +2129,20 @@ int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result*
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (long long)p[a].m * p[a].n > (long long)p[b].m * p[b].n;
   });
+  bool all_plain = true;                // problems (P): the device-resident iteration takes them
+  for (int i = 0; i < count && all_plain; ++i) all_plain = p[i].var_kind == nullptr;
+  if (all_plain && h->use_dev_ipm && h->use_graphs && h->opt.precision_mode == 0 && h->opt.reuse_pcg == 0) {
+    // device-resident iterations: no lock step (see batch_device)
+    const int rc = batch_device(h, count, p, r, order, want);
+    if (rc < 0) return rc;
+    int worst_err = NYS_OK, worst_warn = NYS_OK;
+    for (int i = 0; i < count; ++i) {
+      if (r[i].status < worst_err) worst_err = r[i].status;
+      if (r[i].status > worst_warn) worst_warn = r[i].status;
+    }
+    if (worst_err < 0) return fail(h, worst_err, "nys_solve_batched: at least one problem failed");
+    return worst_warn;
+  }
   for (int g0 = 0; g0 < count; g0 += want) {
     const int G = std::min(want, count - g0);
     std::vector<IpmRun> runs(G);
@@ -1831,22 +2221,41 @@ int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result*
     if (P.var_kind)
       return fail(h, NYS_ERR_ARG, "nys_adjoint: problem %d has free or box-constrained variables", i);
     const double* A = static_cast<const double*>(P.A);
-    const int ell = std::min(h->ell_cap, m);
+    int ell = std::min(h->ell_cap, m);
     const double* g = dL_dx + on;
     CK(cudaMemsetAsync(h->si, 0, sizeof(int) * SI_COUNT, h->st));
-    // final D and a fresh Nystrom factor of N at the solution
+    // final D
     CK(scaling_f64(h->st, n, R.x, R.z, P.q, R.rho, h->D));
-    CK(gaussian_omega(h->st, h->opt.seed, R.ipm_iters + 1, m, ell, h->Om, h->ld));
-    CK(sketch_f64(h->st, m, n, A, P.lda, h->D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf,
-                  h->split_cap));
-    CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red, h->cw,
-                        h->num_sms));
+    // The Nystrom factor of the solve's last IPM iteration, when this handle
+    // (or the batch worker that solved the problem) still holds it: N there
+    // differs from N at the solution only by the last, converged step, so it
+    // preconditions the adjoint system as well (the PCG below solves to eta
+    // whatever the factor).  Otherwise a fresh factor of N at the solution.
+    const double* U = h->U;
+    const double* lamh = h->lamh;
+    int ldu = h->ld;
+    const nys_solver* src = nullptr;
+    if (h->fac_A == A && h->fac_m == m) src = h;
+    for (nys_solver* w : h->workers)
+      if (!src && w->fac_A == A && w->fac_m == m) src = w;
+    if (src) {
+      U = src->U;
+      lamh = src->lamh;
+      ldu = src->ld;
+      ell = src->fac_ell;
+    } else {
+      CK(gaussian_omega(h->st, h->opt.seed, R.ipm_iters + 1, m, ell, h->Om, h->ld));
+      CK(sketch_f64(h->st, m, n, A, P.lda, h->D, ell, h->Om, h->ld, h->Y, h->T, h->ld_t, h->split_buf,
+                    h->split_cap));
+      CK(nystrom_core_f64(h->st, m, ell, h->Y, h->Om, h->ld, h->U, h->lamh, h->sd, h->si, h->red, h->cw,
+                          h->num_sms));
+    }
     // (N + delta I) lam2 = A (D .* g)
     CK(vmul_f64(h->st, n, h->D, g, h->t_n));
     CK(gemv_n_f64(h->st, m, n, A, P.lda, h->t_n, 0.0, nullptr, h->xi, nullptr, nullptr, h->split_buf,
                   h->split_cap));
     int it = 0;
-    int rc = run_pcg(h, m, n, A, P.lda, h->D, R.delta, ell, h->U, h->ld, h->lamh, h->xi, h->dyp, eta,
+    int rc = run_pcg(h, m, n, A, P.lda, h->D, R.delta, ell, U, ldu, lamh, h->xi, h->dyp, eta,
                      h->opt.max_pcg_iter, -1, &it);
     if (rc < 0) return rc;
     if (rc > worst) worst = rc;
@@ -1908,6 +2317,10 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r) {
   // a phase that returns an error without ending the run hit a CUDA failure:
   // leave at once, as every other entry point does
   int rc = NYS_OK;
+  if (run.device_eligible()) {
+    rc = run.device_solve();
+    if (rc < 0) return rc;
+  }
   while (!run.done) {
     if ((rc = run.top()) < 0 && !run.done) return rc;
     if (run.done) break;

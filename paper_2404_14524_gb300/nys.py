@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("precision_mode", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("reg_floor", ctypes.c_double),
                 ("forced_pcg_iters", ctypes.POINTER(ctypes.c_int)), ("n_forced_pcg", ctypes.c_int),
-                ("forced_ipm_iters", ctypes.c_int), ("start_mode", ctypes.c_int), ("reuse_pcg", ctypes.c_int)]
+                ("forced_ipm_iters", ctypes.c_int), ("start_mode", ctypes.c_int), ("reuse_pcg", ctypes.c_int),
+                ("adapt_cost", ctypes.c_int), ("ell_min", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -76,7 +77,8 @@ class Result(ctypes.Structure):
                 ("delta", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("pcg_seconds", ctypes.c_double), ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
                 ("pcg_log_len", ctypes.c_int), ("w", ctypes.c_void_p), ("s", ctypes.c_void_p),
-                ("sketches", ctypes.c_int), ("peu_ref_p", ctypes.c_double), ("peu_ref_d", ctypes.c_double)]
+                ("sketches", ctypes.c_int), ("peu_ref_p", ctypes.c_double), ("peu_ref_d", ctypes.c_double),
+                ("ell_log", ctypes.POINTER(ctypes.c_int)), ("ell_log_cap", ctypes.c_int), ("ell_log_len", ctypes.c_int)]
 
 
 _lib = None
@@ -461,11 +463,12 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     if peu_ref is not None:
         p.has_peu_ref, p.peu_ref_p, p.peu_ref_d = 1, float(peu_ref[0]), float(peu_ref[1])
     log = (ctypes.c_int * pcg_log_cap)()
+    elog = (ctypes.c_int * pcg_log_cap)()
     w, s = (mk(n), mk(n)) if kind is not None else (None, None)
     r = Result(x=x.data_ptr(), y=y.data_ptr(), z=z.data_ptr(),
                lam=lam.data_ptr() if lam is not None else None,
                zeta=zeta.data_ptr() if zeta is not None else None,
-               pcg_log=log, pcg_log_cap=pcg_log_cap,
+               pcg_log=log, pcg_log_cap=pcg_log_cap, ell_log=elog, ell_log_cap=pcg_log_cap,
                w=w.data_ptr() if w is not None else None, s=s.data_ptr() if s is not None else None)
     rc = lib().nys_solve(h.h, ctypes.byref(p), ctypes.byref(r))
     if check:
@@ -475,6 +478,7 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
                                        "seconds", "pcg_seconds", "sketches", "peu_ref_p",
                                        "peu_ref_d")}
     info["pcg_log"] = list(log[: r.pcg_log_len])
+    info["ell_log"] = list(elog[: r.ell_log_len])
     if want_pmm:
         info["lam"], info["zeta"] = lam, zeta
     if kind is not None:

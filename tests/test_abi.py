@@ -135,8 +135,8 @@ def test_plain_c_program_links_and_gets_argument_errors(libpath):
 int main(void) {
   nys_options o;
   nys_default_options(&o);
-  printf("%g %d %d %d %g %g %d %d %d\n", o.tol, o.ell, o.max_ipm_iter, o.max_pcg_iter, o.rho0, o.reg_floor,
-         o.forced_ipm_iters, o.start_mode, o.reuse_pcg);
+  printf("%g %d %d %d %g %g %d %d %d %d %d\n", o.tol, o.ell, o.max_ipm_iter, o.max_pcg_iter, o.rho0, o.reg_floor,
+         o.forced_ipm_iters, o.start_mode, o.reuse_pcg, o.adapt_cost, o.ell_min);
   nys_handle h = 0;
   printf("%d %d %d\n", nys_create(0, &o, 10, 20, 0, 0), nys_create(&h, &o, 0, 20, 0, 0),
          nys_create(&h, 0, 10, 20, 0, 0));
@@ -167,7 +167,7 @@ int main(void) {
                         "-Wl,-rpath," + libdir], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True, env=env, timeout=120).stdout
     lines = out.split("\n")
-    assert lines[0].split() == ["1e-06", "20", "200", "1000", "8", "5e-10", "-1", "0", "0"]
+    assert lines[0].split() == ["1e-06", "20", "200", "1000", "8", "5e-10", "-1", "0", "0", "0", "0"]
     assert lines[1].split() == ["-1", "-1", "-1"]
     assert lines[2] == "-1"
     assert lines[3] in ("0", "-2")

@@ -91,3 +91,37 @@ def test_autograd_function_matches_finite_differences(nys, seed):
         an = float((A.grad.cpu().numpy() * dA).sum() + b.grad.cpu().numpy() @ db +
                    c.grad.cpu().numpy() @ dc + q.grad.cpu().numpy() @ dq)
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (fd, an)
+
+
+def test_adjoint_reuses_the_last_factor_of_the_solve(nys):
+    """When the handle (or the batch worker that solved the problem) still
+    holds the solve's last Nystrom factor for the same A, the adjoint takes it
+    instead of sketching N again (fewer kernel launches); the gradients agree
+    with the re-sketched path and with the dense KKT solve."""
+    m, n = 128, 512
+    qp = synth.gaussian_qp(777, m, n)
+    xt = np.random.default_rng(1).uniform(0, 1, n)
+    A = T(qp.A)
+    h = nys.Handle(m, n, ell=32, tol=1e-8, seed=3)
+    x, y, z, info = nys.nys_solve(h, A, T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))
+    g = T(2 * (x.cpu().numpy() - xt))
+    l0 = nys.nys_kernel_launches()
+    G1 = nys.nys_adjoint(h, A, T(qp.q), x, y, z, info, g, eta=1e-13)          # same A: reuse
+    l1 = nys.nys_kernel_launches()
+    G2 = nys.nys_adjoint(h, A.clone(), T(qp.q), x, y, z, info, g, eta=1e-13)  # other pointer: re-sketch
+    l2 = nys.nys_kernel_launches()
+    assert l1 - l0 < l2 - l1
+    xs, ys, zs = (t.cpu().numpy() for t in (x, y, z))
+    W = O.kkt_adjoint(qp.A, xs, ys, zs, qp.q, info["rho"], info["delta"], g.cpu().numpy())
+    for k, want in (("c", W.c), ("b", W.b), ("q", W.q), ("A", W.A)):
+        a, b = G1[k].cpu().numpy(), G2[k].cpu().numpy()
+        assert np.linalg.norm(a - want) <= 1e-6 * np.linalg.norm(want)
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(want)
+    # forward through the batching form: the worker's factor is found
+    hb = nys.Handle(m, n, ell=32, tol=1e-8, seed=3, max_batch=2)
+    (xb, yb, zb, ib), = nys.nys_solve_batched(hb, [(A, T(qp.b), T(qp.c), T(qp.q), T(qp.x0), T(qp.y0), T(qp.z0))])
+    l3 = nys.nys_kernel_launches()
+    G3 = nys.nys_adjoint(hb, A, T(qp.q), xb, yb, zb, ib, g, eta=1e-13)
+    l4 = nys.nys_kernel_launches()
+    assert l4 - l3 < l2 - l1
+    assert np.linalg.norm(G3["A"].cpu().numpy() - W.A) <= 1e-6 * np.linalg.norm(W.A)
