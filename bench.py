@@ -640,6 +640,7 @@ def main():
             "config": {"workload": args.workload, "desc": w["desc"], "form": form, "qps_per_step": per_step,
                        "start": "practical initial point" if args.practical_start else "workload interior point",
                        "max_batch": args.max_batch if form in ("batch", "diff") else None,
+                       "inflight_tuned": nys.nys_batch_inflight(h) if form in ("batch", "diff") else None,
                        "reuse_pcg": args.reuse_pcg,
                        "m_max": mmax, "n_max": nmax, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB)" if a_bytes > 129e6

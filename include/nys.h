@@ -194,6 +194,8 @@ typedef struct {
     int* ell_log;                 /* optional host array: sketch size of each factor  */
     int ell_log_cap;              /*   built, in order (capacity in entries)           */
     int ell_log_len;              /* entries written                                   */
+    int device_iteration;         /* 1: the device-resident iteration ran (one graph  */
+                                  /*   launch per IPM iteration), 0: host phases       */
 } nys_result;
 
 /* Fill *opt with the defaults listed above. */
@@ -212,14 +214,28 @@ int nys_create(nys_handle* h, const nys_options* opt, int max_m, int max_n, int 
 int nys_solve(nys_handle h, const nys_problem* p, nys_result* r);
 
 /* Solve `count` independent QPs (the batching form), each exactly as
- * nys_solve would, with up to max_batch of them in flight at once: a pool of
- * host worker threads, each owning a private solver (workspace, CUDA stream,
- * cached PCG graph) sized for the handle's max_m x max_n, pulls problems from
- * a shared queue.  p[i] and r[i] follow nys_solve's conventions (device or
+ * nys_solve would, with up to max_batch of them in flight at once; each
+ * in-flight problem owns a private worker solver (workspace, CUDA stream,
+ * cached graphs) sized for the handle's max_m x max_n.  When every problem is
+ * of kind (P) and the form is FP64, each worker advances its problem with the
+ * device-resident iteration (one graph launch per IPM iteration) at its own
+ * pace, one host thread keeping the workers fed, and the number in flight is
+ * autotuned on the first call (see nys_batch_inflight); otherwise the
+ * problems run in lock-step groups whose PCG solves share thread-block
+ * cluster launches.  p[i] and r[i] follow nys_solve's conventions (device or
  * host memory per problem).  The handle must have been created with
  * max_batch >= 1.  Returns the worst status (negative errors first); each
- * r[i].status holds its own.  All work is complete on return. */
+ * r[i].status holds its own.  All work is complete on return.  A problem's
+ * results do not depend on the batch it is in or on the number in flight. */
 int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result* r);
+
+/* Problems in flight chosen for this handle's batches by timed trials (0
+ * until a batch of at least 128 problems with max_batch >= 16 has run on the
+ * device-resident path): in-flight counts of 8, 16, 24, 32, 48, 64, ... are
+ * scored by the PCG work completed per second over 0.8 s each, a larger
+ * count kept only when it beats the best by 3 %.  Untuned batches run
+ * max_batch at once; NYS_BATCH_TUNE=0 keeps max_batch. */
+int nys_batch_inflight(nys_handle h);
 
 int nys_destroy(nys_handle h);
 

@@ -140,6 +140,8 @@ struct nys_solver {
   int ik_m = 0, ik_n = 0, ik_ell = 0, ik_C = 0, ik_as = 0;
   unsigned ipm_kernels_top = 0, ipm_kernels_body = 0;
   bool use_dev_ipm = true;             // NYS_DEVICE_IPM=0 keeps the host-driven iteration
+  int tuned_inflight = 0;              // batching form: problems in flight chosen by the autotuner
+  int trace_tune = 0;                  // NYS_TRACE_TUNE=1: the autotuner's trials on stderr
   // batching form: worker solvers (created on first use), one per in-flight QP
   int max_batch = 0;
   std::vector<nys_solver*> workers;
@@ -895,6 +897,7 @@ int IpmRun::start(nys_solver* h_, const nys_problem* p_, nys_result* r_) {
   r->refine_steps = 0;
   r->pcg_log_len = 0;
   r->ell_log_len = 0;
+  r->device_iteration = 0;
   h->fac_A = nullptr;          // U / lamh are about to be overwritten
   r->pcg_seconds = 0.0;
   r->sketches = 0;
@@ -1450,6 +1453,7 @@ int IpmRun::device_step() {
 // Results of a finished device-resident run (stream synchronised).
 int IpmRun::device_collect() {
   const IpmDev& hd = *h->h_ipmd;
+  r->device_iteration = 1;
   const int nlog = std::min(hd.solves, h->dev_log_cap);
   if (nlog > 0) {
     CK(cudaMemcpyAsync(h->h_pcglog, h->d_pcglog, sizeof(int) * nlog, cudaMemcpyDeviceToHost, h->st));
@@ -1785,6 +1789,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
   if (const char* env = std::getenv("NYS_JACOBI_F32")) h->cw.f32_start = (env[0] != '0');
   if (const char* env = std::getenv("NYS_DEVICE_IPM")) h->use_dev_ipm = (env[0] != '0');
+  if (const char* env = std::getenv("NYS_TRACE_TUNE")) h->trace_tune = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||
       cudaStreamSynchronize(h->st) != cudaSuccess) {
     cudaFree(h->arena);
@@ -2021,16 +2026,35 @@ void host_run(IpmRun& run) {
 // its own pace (no lock step: a short solve does not wait for a long one),
 // and a worker takes the next problem as soon as its current one finishes.
 // Problems the path does not take run on the host-driven phases.
+//
+// How many problems are in flight is autotuned: the streams reach the GPU
+// through a limited number of hardware queues (CUDA_DEVICE_MAX_CONNECTIONS),
+// and beyond it problems only queue behind each other (measured on 256 QPs of
+// m <= 1024 with 32 queues: 13.8 QP/s with 32 in flight, 11.7 with 64, 9.9
+// with 128).  While a handle has no tuned value, the first call tries
+// in-flight counts of 8, 16, 24, 32, 48, 64, ... (up to max_batch) for
+// kTuneWindow seconds each after kTuneSettle seconds of settling, scores
+// each by the PCG work it completed per second (PCG iterations x m x n),
+// stops after two counts that do not beat the best by kTuneMargin, and keeps
+// the best for the rest of the call and for later calls
+// (nys_batch_inflight reports it).  Batches of fewer than 128 problems are
+// too short to tune and run max_batch at once.  Each problem's arithmetic depends on its
+// own launch plan only, so the choice never changes a result.
+constexpr double kTuneSettle = 0.1;
+constexpr double kTuneWindow = 0.8;
+constexpr double kTuneMargin = 1.03;   // a larger count must beat the best by 3 %
+
 int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, const std::vector<int>& order,
                  int want) {
   std::vector<IpmRun> runs(want);
-  std::vector<int> busy(want, 0);
+  std::vector<int> busy(want, 0), seen(want, 0);
   int next = 0, active = 0;
   auto begin = [&](int t) -> bool {
     while (next < count) {
       const int pi = order[next++];
       IpmRun& run = runs[t];
       run = IpmRun();
+      seen[t] = 0;
       if (run.start(h->workers[t], &p[pi], &r[pi]) != NYS_OK) {
         r[pi].status = run.status;
         continue;
@@ -2053,16 +2077,41 @@ int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, 
     }
     return false;
   };
-  for (int t = 0; t < want; ++t)
+  // in-flight autotuning (see above)
+  std::vector<int> cand;
+  bool tuning = false;
+  int limit = want;
+  bool tune_env = true;
+  if (const char* env = std::getenv("NYS_BATCH_TUNE")) tune_env = env[0] != '0';
+  if (h->tuned_inflight > 0) {
+    limit = std::min(h->tuned_inflight, want);
+  } else if (tune_env && want >= 16 && count >= 128) {
+    for (int c : {8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512})
+      if (c < want) cand.push_back(c);
+    cand.push_back(want);
+    tuning = true;
+    limit = cand[0];
+  }
+  using clk = std::chrono::steady_clock;
+  auto now = [] { return std::chrono::duration<double>(clk::now().time_since_epoch()).count(); };
+  size_t ci = 0;
+  double t_change = now(), work = 0.0, best_rate = -1.0;
+  int best = limit, worse = 0;
+  for (int t = 0; t < limit; ++t)
     if (begin(t)) { busy[t] = 1; ++active; }
   while (active > 0) {
     bool progressed = false;
+    const double t_now = now();
     for (int t = 0; t < want; ++t) {
       if (!busy[t]) continue;
       const cudaError_t q = cudaStreamQuery(h->worker_streams[t]);
       if (q == cudaErrorNotReady) continue;
       progressed = true;
       IpmRun& run = runs[t];
+      // PCG work completed since the last read-back of this problem
+      const int tot = h->workers[t]->h_ipmd->pcg_total;
+      if (tuning && t_now >= t_change + kTuneSettle) work += (double)(tot - seen[t]) * run.m * (double)run.n;
+      seen[t] = tot;
       int rc = q == cudaSuccess ? run.device_step() : NYS_ERR_CUDA;
       if (rc == 1) continue;              // the next iteration is in flight
       if (rc < 0) {
@@ -2074,10 +2123,32 @@ int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, 
       run.finish();
       busy[t] = 0;
       --active;
-      if (begin(t)) { busy[t] = 1; ++active; }
+      if (t < limit && begin(t)) { busy[t] = 1; ++active; }
     }
+    if (tuning && t_now >= t_change + kTuneSettle + kTuneWindow) {
+      const double rate = work / kTuneWindow;
+      if (h->trace_tune)
+        std::fprintf(stderr, "[nys] batch in flight %d: %.3e PCG work/s (next problem %d of %d, active %d)\n",
+                     limit, rate, next, count, active);
+      if (best_rate < 0.0 || rate > kTuneMargin * best_rate) { best_rate = rate; best = limit; worse = 0; }
+      else ++worse;
+      ++ci;
+      if (ci >= cand.size() || worse >= 2 || next >= count) {
+        tuning = false;
+        limit = best;
+        h->tuned_inflight = best;
+      } else {
+        limit = cand[ci];
+      }
+      work = 0.0;
+      t_change = now();
+    }
+    // fill the slots a larger limit opened
+    for (int t = 0; t < limit && next < count; ++t)
+      if (!busy[t] && begin(t)) { busy[t] = 1; ++active; }
     if (!progressed) std::this_thread::yield();
   }
+  if (tuning && best_rate >= 0.0) h->tuned_inflight = best;
   return NYS_OK;
 }
 
@@ -2275,6 +2346,11 @@ int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result*
     omn += (size_t)m * n;
   }
   return worst;
+}
+
+int nys_batch_inflight(nys_handle h) {
+  if (!h) return NYS_ERR_ARG;
+  return h->tuned_inflight;
 }
 
 int nys_pcg_route(nys_handle h, int m, int n, int ell) {

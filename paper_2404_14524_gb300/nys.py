@@ -78,7 +78,8 @@ class Result(ctypes.Structure):
                 ("pcg_seconds", ctypes.c_double), ("pcg_log", ctypes.POINTER(ctypes.c_int)), ("pcg_log_cap", ctypes.c_int),
                 ("pcg_log_len", ctypes.c_int), ("w", ctypes.c_void_p), ("s", ctypes.c_void_p),
                 ("sketches", ctypes.c_int), ("peu_ref_p", ctypes.c_double), ("peu_ref_d", ctypes.c_double),
-                ("ell_log", ctypes.POINTER(ctypes.c_int)), ("ell_log_cap", ctypes.c_int), ("ell_log_len", ctypes.c_int)]
+                ("ell_log", ctypes.POINTER(ctypes.c_int)), ("ell_log_cap", ctypes.c_int), ("ell_log_len", ctypes.c_int),
+                ("device_iteration", ctypes.c_int)]
 
 
 _lib = None
@@ -114,6 +115,7 @@ _SIGS = {
     "nys_step_length": (_I, [_P, _I, _P, _P, ctypes.POINTER(_D)]),
     "nys_gemm_bf16": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL]),
     "nys_solve_batched": (_I, [_P, _I, ctypes.POINTER(Problem), ctypes.POINTER(Result)]),
+    "nys_batch_inflight": (_I, [_P]),
     "nys_adjoint": (_I, [_P, _I, ctypes.POINTER(Problem), ctypes.POINTER(Result), _P, _D, _P, _P, _P, _P]),
 }
 
@@ -476,7 +478,7 @@ def nys_solve(h: Handle, A, b, c, q, x0, y0, z0, pcg_log_cap: int = 4096, check:
     info = {k: getattr(r, k) for k in ("status", "ipm_iters", "pcg_iters_total", "refine_steps",
                                        "rel_primal", "rel_dual", "mu", "rel_gap", "rho", "delta",
                                        "seconds", "pcg_seconds", "sketches", "peu_ref_p",
-                                       "peu_ref_d")}
+                                       "peu_ref_d", "device_iteration")}
     info["pcg_log"] = list(log[: r.pcg_log_len])
     info["ell_log"] = list(elog[: r.ell_log_len])
     if want_pmm:
@@ -551,6 +553,11 @@ def qp_solve(A, b, c, q, x0, y0, z0, handle, eta: float = 1e-12):
     return NysQPFunction.apply(A, b, c, q, x0, y0, z0, handle, eta)
 
 
+def nys_batch_inflight(h: Handle) -> int:
+    """Problems in flight the handle's batch autotuner chose (0: not tuned yet)."""
+    return int(lib().nys_batch_inflight(h.h))
+
+
 def nys_solve_batched(h: Handle, problems, check: bool = True, forced=None, pcg_log_cap: int = 4096):
     """Solve a list of QPs [(A, b, c, q, x0, y0, z0[, ell[, box]]), ...]
     (device tensors; optional per-problem sketch size, 0 = the handle's; box
@@ -597,7 +604,7 @@ def nys_solve_batched(h: Handle, problems, check: bool = True, forced=None, pcg_
     for i, (x, y, z, w, s) in enumerate(outs):
         info = {f: getattr(R[i], f) for f in ("status", "ipm_iters", "pcg_iters_total", "refine_steps", "rel_primal",
                                               "rel_dual", "mu", "rel_gap", "rho", "delta", "seconds",
-                                              "pcg_seconds", "sketches")}
+                                              "pcg_seconds", "sketches", "device_iteration")}
         info["pcg_log"] = list(logs[i][: R[i].pcg_log_len])
         if w is not None:
             info["w"], info["s"] = w, s
