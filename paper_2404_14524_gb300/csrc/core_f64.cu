@@ -569,12 +569,16 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
 // nearly orthogonal columns, so the FP64 Jacobi that follows needs two or
 // three sweeps instead of six to nine.  B is scaled by a power of two so that
 // its largest column norm is about 1 (the FP32 copy keeps small columns in
-// range).  The FP32 sweeps stop when no pair needs a rotation at the FP32
-// threshold kJ32Tol or after max_sweeps.
+// range).  The FP32 sweeps stop when no pair needs a rotation or after
+// max_sweeps; a pair needs one when its inner product exceeds kJ32Tol times
+// the geometric mean of its squared norms and also kJ32Noise times the
+// largest squared column norm (below that, FP32 rounding of the big columns
+// dominates and the FP64 sweeps must decide anyway).
 constexpr int kJ32T = 512;
 constexpr int kJ32W = kJ32T / 32;
 constexpr int kJ32MaxElems = 40960;      // m * ell floats of the copy (160 KB)
 constexpr float kJ32Tol = 1e-5f;
+constexpr float kJ32Noise = 1e-6f;
 
 __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, const double* __restrict__ B, int ld,
                                                             double* __restrict__ V, int max_sweeps,
@@ -605,6 +609,20 @@ __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, cons
     F[e] = (float)(B[(size_t)c * ld + i] * scale);
   }
   for (int e = tid; e < ell * ell; e += kJ32T) V32[e] = (e % ell == e / ell) ? 1.0f : 0.0f;
+  __syncthreads();
+  // largest squared column norm of the scaled copy: the FP32 noise level
+  float cm = 0.0f;
+  for (int c = wid; c < ell; c += kJ32W) {
+    float a = 0.0f;
+    for (int i = lane; i < m; i += 32) a = fmaf(F[(size_t)c * m + i], F[(size_t)c * m + i], a);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    cm = fmaxf(cm, a);
+  }
+  if (lane == 0) colmax[wid] = cm;
+  __syncthreads();
+  cm = 0.0f;
+  for (int w = 0; w < kJ32W; ++w) cm = fmaxf(cm, colmax[w]);
+  const float noise = kJ32Noise * cm;
   const int lp = ell + (ell & 1);
   const int npairs = lp / 2;
   const int L = lp - 1;
@@ -631,7 +649,7 @@ __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, cons
             be += __shfl_xor_sync(0xffffffffu, be, o);
             ga += __shfl_xor_sync(0xffffffffu, ga, o);
           }
-          if (al > 0.0f && be > 0.0f && fabsf(ga) > kJ32Tol * sqrtf(al) * sqrtf(be)) {
+          if (al > 0.0f && be > 0.0f && fabsf(ga) > kJ32Tol * sqrtf(al) * sqrtf(be) && fabsf(ga) > noise) {
             const float d = be - al;
             const float h = fmaf(d, d, 4.0f * ga * ga);
             const float t = (2.0f * ga) * copysignf(1.0f, d == 0.0f ? 1.0f : d) / (fabsf(d) + sqrtf(h));
@@ -862,7 +880,7 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
                              (int)(sizeof(float) * (kJ32MaxElems + 32 * 32)));
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_jacobi_f32_start<<<1, kJ32T, sm, st>>>(m, ell, cw.Ynu, ld, cw.R, 12, err);
+    k_jacobi_f32_start<<<1, kJ32T, sm, st>>>(m, ell, cw.Ynu, ld, cw.R, 8, err);
     e = gemm_f64(st, m, ell, ell, cw.Ynu, 1, ld, cw.R, 1, ell, nullptr, cw.B2, 1, ld, cw.split_buf,
                  cw.split_cap);
     if (e != cudaSuccess) return e;
