@@ -823,7 +823,8 @@ def config3_record(nys, dev, stream, seed, cpu=True):
 def operator_rooflines(nys, dev, stream):
     """The operator GEMV pairs at the large workload shapes (inputs far larger
     than L2, random entries): FP64 at m=5000, n=20000, BF16 and FP8 (E4M3,
-    row scales) at m=20000, n=100000."""
+    row scales) at m=20000, n=100000; and the sketch's two tensor-core
+    products at m=20000, n=100000, ell=400."""
     import torch
     out = {}
     g = torch.Generator(device=dev).manual_seed(0)
@@ -856,6 +857,9 @@ def operator_rooflines(nys, dev, stream):
         torch.cuda.synchronize(dev)
         op_s = f0.elapsed_time(f1) / reps / 1e3
         h.close()
+        hs = nys.Handle(m, n, ell=400, precision_mode=1, stream=stream)
+        out["sketch_gemm_20000x100000x400"] = sketch_gemm_record(nys, hs, A, AT, stream)
+        hs.close()
         del A, AT
     hbm_peak, _, src = measured_peaks()
     bytes_alg = 2.0 * m * n * 2 + 4.0 * (3 * m + 2 * n)
@@ -868,6 +872,48 @@ def operator_rooflines(nys, dev, stream):
                                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})"}
     torch.cuda.empty_cache()
     return out
+
+
+def sketch_gemm_record(nys, h, A, AT, stream, ell=400, reps=10):
+    """The precision form's two sketch products (Algorithm 1, second step) at
+    m=20000, n=100000, ell=400: T = A^T Omega (M = n, K = m) and Y = A T'
+    (M = m, K = n), 2 m n ell flop each, BF16 operands with FP32
+    accumulation, inputs far larger than L2.  Each product is timed alone with
+    CUDA events on `stream` over `reps` calls of nys_gemm_bf16 (the product
+    and, where tiles are split across CTA pairs, the fixed-order sum of their
+    partials; one host synchronisation per call is inside the timed region)."""
+    import torch
+    dev = A.device
+    m, n = A.shape
+    g = torch.Generator(device=dev).manual_seed(1)
+    Om = torch.randn(ell, m, generator=g, device=dev).to(torch.bfloat16)
+    Tt = (torch.randn(ell, n, generator=g, device=dev) / 100).to(torch.bfloat16)
+    _, peak, src = measured_peaks()
+    prods = {}
+    for key, X, B in (("T = A^T Omega", AT, Om), ("Y = A T'", A, Tt)):
+        out = torch.empty((ell, X.shape[0]), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            nys.nys_gemm_bf16(h, X, B, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            nys.nys_gemm_bf16(h, X, B, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = e0.elapsed_time(e1) / reps / 1e3
+        fl = 2.0 * X.shape[0] * X.shape[1] * ell
+        prods[key] = {"M": X.shape[0], "K": X.shape[1], "N": ell, "ms": sec * 1e3, "achieved": fl / sec / 1e12,
+                      "frac": fl / sec / 1e12 / peak}
+        del out
+    tot_fl = sum(2.0 * v["M"] * v["K"] * ell for v in prods.values())
+    tot_s = sum(v["ms"] for v in prods.values()) / 1e3
+    tr = traffic_record("umma_bf16.cu", "sketch_gemm_pair_8000x40000")
+    return {"bound": "tensor", "achieved": tot_fl / tot_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": tot_fl / tot_s / 1e12 / peak, "products": prods,
+            "traffic_ncu_8000x40000x400": None if tr is None else {
+                "bytes_per_launch": tr["bytes_per_launch"], "algorithmic_bytes": tr["algorithmic_bytes"]},
+            "kernel": "k_umma_gemm_pair (tcgen05.mma.cta_group::2) + k_pair_reduce",
+            "peak_source": f"MEASURED_PEAKS.json bf16_tflops, burst ({src})"}
 
 
 def time_fp8_operator(nys, h, A32, stream, reps=20):

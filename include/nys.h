@@ -338,7 +338,12 @@ int nys_gaussian(nys_handle h, unsigned long long seed, int k, int m, int ell, d
                  int ld);
 
 /* Sketch Y = N Omega = A (D .* (A^T Omega)) (Algorithm 1, second step).
- * Omega, Y: device m x ell (column-major, leading dimension ld); D: device n. */
+ * Omega, Y: device m x ell (column-major, leading dimension ld); D: device n.
+ * a_dtype NYS_F64: FP64 arithmetic.  a_dtype NYS_F32 (precision-form handle
+ * only, else NYS_ERR_ARG): the precision form's sketch on the tensor cores --
+ * A (FP32) and Omega rounded to BF16 (Omega via FP32), T = A^T Omega with FP32
+ * accumulation, T' = BF16(D .* T), Y = A T' with FP32 accumulation, widened
+ * to FP64; Omega is not modified. */
 int nys_sketch(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
                const double* D, int ell, const double* Omega, double* Y, int ld);
 
@@ -414,8 +419,14 @@ int nys_newton(nys_handle h, int m, int n, int a_dtype, const void* A, long long
  * are of this shape (A^T Omega with A^T stored row-major, and A T').
  * A: M x K, B: N x K, both BF16 row-major with K contiguous, leading
  * dimensions multiples of 8 elements, 16-byte aligned; C: FP32 column-major
- * M x N, ldc >= M.  N <= 512.  Device pointers.  The split-K partial sums use
- * the handle's workspace: NYS_ERR_ARG if they do not fit (M * N * splits). */
+ * M x N, ldc >= M.  N <= 512.  Device pointers.  Kernel: a CTA pair per
+ * 256-row stripe (tcgen05.mma.cta_group::2) with the k-blocks split evenly
+ * over the resident pairs, partial tiles summed in a fixed order; or, where
+ * clusters of two cannot run or the partial tiles do not fit the handle's
+ * workspace, one CTA per 128-row stripe with split-K.  The environment
+ * variable NYS_UMMA_PAIR=0 / 1 forces the one-CTA / the pair kernel (1: a
+ * CUDA error when the pair kernel cannot run).  NYS_ERR_ARG if M x N (padded)
+ * exceeds the handle's workspace. */
 int nys_gemm_bf16(nys_handle h, int M, int N, int K, const void* A, long long lda, const void* B,
                   long long ldb, float* C, long long ldc);
 

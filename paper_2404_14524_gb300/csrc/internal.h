@@ -144,17 +144,18 @@ cudaError_t quantize_fp8(cudaStream_t st, int rows, int cols, const float* A, lo
                          double* s64, void* Q, long long ldq, void* QT, long long ldqt);
 
 // ---------------------------------------------------------------- tcgen05 BF16 GEMM
-// part[z][c][r] = sum_{k in split z} A[r, k] B[c, k]; A: M x K, B: N x K, both
-// BF16 row-major (K contiguous, leading dimensions multiples of 8), N <= 512.
-// *S_out receives the number of K splits used (part must hold S*Npad*M floats,
-// Npad = N rounded up to 16).
+// out[c * ldo + r] = op(sum_k A[r, k] B[c, k]) for r < M, c < N; A: M x K,
+// B: N x K, both BF16 row-major (K contiguous, leading dimensions multiples
+// of 8), N <= 512, FP32 accumulation.  mode 0: FP32 out; mode 1: scaled by
+// D[r] (FP64) and stored as BF16.  The CTA-pair kernel (M = 256 per pair,
+// stream-K over k-blocks) runs when clusters of two can be launched and
+// `part` holds its partial tiles, else the one-SM kernel with split-K;
+// *kernel_used (if given) receives 2 or 1.  part_cap is in floats; size it
+// with umma_part_elems.
 size_t umma_part_elems(int M, int N, int K, int num_sms);
 cudaError_t umma_gemm_bf16(cudaStream_t st, int M, int N, int K, const void* A, long long lda,
-                           const void* B, long long ldb, float* part, size_t part_cap, int num_sms,
-                           int* S_out, int* err);
-// out[c*ldo + r] = sum_z part[z][c][r]: mode 0 FP32 out; mode 1 scaled by D[r], BF16 out.
-cudaError_t umma_reduce(cudaStream_t st, int M, int N, int S, const float* part, int mode,
-                        const double* D, void* out, long long ldo);
+                           const void* B, long long ldb, float* part, size_t part_cap, int num_sms, int mode,
+                           const double* D, void* out, long long ldo, int* err, int* kernel_used = nullptr);
 
 // ---------------------------------------------------------------- PCG / P^{-1}
 struct PcgWork {

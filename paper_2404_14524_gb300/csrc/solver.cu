@@ -630,6 +630,22 @@ int op_Aty(nys_solver* h, const Prob& P, const double* y, const double* scale, d
   return NYS_OK;
 }
 
+// Precision-form sketch from Omega in h->Om (FP64, leading dimension h->ld)
+// and the BF16 copies of A in h->Ab / h->AbT: Omega is rounded to BF16 in
+// place (both views then hold the same test matrix), T = A^T Omega on the
+// tensor cores with T' = BF16(D .* T) written by the GEMM, Y = A T' (FP32
+// accumulation) widened to FP64 into Y (leading dimension ldy).
+int lp_sketch(nys_solver* h, int m, int n, int ell, const double* D, double* Y, int ldy) {
+  CK(round_panel_bf16(h->st, m, ell, h->Om, h->ld, h->Omb, (int)h->ld_om));
+  int* err = h->si + SI_ERR;
+  CK(umma_gemm_bf16(h->st, n, ell, m, h->AbT, h->ld_bt, h->Omb, h->ld_om, h->upart, h->upart_cap, h->num_sms, 1,
+                    D, h->Tb, h->ld_tb, err));
+  CK(umma_gemm_bf16(h->st, m, ell, n, h->Ab, h->ld_b, h->Tb, h->ld_tb, h->upart, h->upart_cap, h->num_sms, 0,
+                    nullptr, h->Y32, h->ld, err));
+  CK(panel_f32_to_f64(h->st, m, ell, h->Y32, h->ld, Y, ldy));
+  return NYS_OK;
+}
+
 // Y = A (D .* (A^T Omega_k)) into h->Y, Omega_k into h->Om (FP64 panels).
 int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D, int ell_stride = 0) {
   const nys_options& o = h->opt;
@@ -639,20 +655,7 @@ int op_sketch(nys_solver* h, const Prob& P, int k, int ell, const double* D, int
                   h->split_cap));
     return NYS_OK;
   }
-  // Omega rounded to BF16 (both views then hold the same test matrix)
-  CK(round_panel_bf16(h->st, P.m, ell, h->Om, h->ld, h->Omb, (int)h->ld_om));
-  int S = 0;
-  int* err = h->si + SI_ERR;
-  // T (n x ell) = A^T Omega on the tensor cores; T' = BF16(D .* T)
-  CK(umma_gemm_bf16(h->st, P.n, ell, P.m, h->AbT, h->ld_bt, h->Omb, h->ld_om, h->upart, h->upart_cap,
-                    h->num_sms, &S, err));
-  CK(umma_reduce(h->st, P.n, ell, S, h->upart, 1, D, h->Tb, h->ld_tb));
-  // Y (m x ell) = A T'
-  CK(umma_gemm_bf16(h->st, P.m, ell, P.n, h->Ab, h->ld_b, h->Tb, h->ld_tb, h->upart, h->upart_cap,
-                    h->num_sms, &S, err));
-  CK(umma_reduce(h->st, P.m, ell, S, h->upart, 0, nullptr, h->Y32, h->ld));
-  CK(panel_f32_to_f64(h->st, P.m, ell, h->Y32, h->ld, h->Y, h->ld));
-  return NYS_OK;
+  return lp_sketch(h, P.m, P.n, ell, D, h->Y, (int)h->ld);
 }
 
 // Precision-form Newton direction: Algorithm 4 with the normal equations
@@ -1907,9 +1910,20 @@ int nys_gaussian(nys_handle h, unsigned long long seed, int k, int m, int ell, d
 int nys_sketch(nys_handle h, int m, int n, int a_dtype, const void* A, long long lda,
                const double* D, int ell, const double* Omega, double* Y, int ld) {
   if (!h) return NYS_ERR_ARG;
-  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || lda < n || a_dtype != NYS_F64 ||
+  if (m <= 0 || n <= 0 || m > h->max_m || n > h->max_n || lda < n || (a_dtype != NYS_F64 && a_dtype != NYS_F32) ||
       ell <= 0 || ell > h->ell_cap || ld < m || !A || !D || !Omega || !Y)
     return fail(h, NYS_ERR_ARG, "nys_sketch: bad argument");
+  if (a_dtype == NYS_F32) {
+    if (!h->lp_arena) return fail(h, NYS_ERR_ARG, "nys_sketch: FP32 A needs a precision-form handle");
+    CK(cudaMemsetAsync(h->si + SI_ERR, 0, sizeof(int), h->st));
+    CK(convert_transpose(h->st, m, n, 0, static_cast<const float*>(A), lda, h->Ab, h->ld_b, h->AbT, h->ld_bt,
+                         nullptr, 0));
+    CK(cudaMemcpy2DAsync(h->Om, sizeof(double) * h->ld, Omega, sizeof(double) * ld, sizeof(double) * m, ell,
+                         cudaMemcpyDeviceToDevice, h->st));
+    const int rc = lp_sketch(h, m, n, ell, D, Y, ld);
+    if (rc != NYS_OK) return rc;
+    return sync_scalars(h, 0);
+  }
   CK(sketch_f64(h->st, m, n, static_cast<const double*>(A), lda, D, ell, Omega, ld, Y, h->T,
                 h->ld_t, h->split_buf, h->split_cap));
   return NYS_OK;
@@ -2369,9 +2383,7 @@ int nys_gemm_bf16(nys_handle h, int M, int N, int K, const void* A, long long ld
   const size_t npad = (size_t)(N + 15) / 16 * 16;
   if (npad * (size_t)M > cap) return fail(h, NYS_ERR_ARG, "nys_gemm_bf16: M x N exceeds the workspace");
   CK(cudaMemsetAsync(h->si + SI_ERR, 0, sizeof(int), h->st));
-  int S = 0;
-  CK(umma_gemm_bf16(h->st, M, N, K, A, lda, B, ldb, part, cap, h->num_sms, &S, h->si + SI_ERR));
-  CK(umma_reduce(h->st, M, N, S, part, 0, nullptr, C, ldc));
+  CK(umma_gemm_bf16(h->st, M, N, K, A, lda, B, ldb, part, cap, h->num_sms, 0, nullptr, C, ldc, h->si + SI_ERR));
   return sync_scalars(h, 0);
 }
 

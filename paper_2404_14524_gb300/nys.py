@@ -305,10 +305,18 @@ def nys_gaussian(h: Handle, seed: int, k: int, m: int, ell: int, out=None):
 
 
 def nys_sketch(h: Handle, A, D, Omega, out=None):
+    """Y = A (D .* (A^T Omega)); A float64 (FP64 sketch) or float32 (the
+    precision form's BF16 tensor-core sketch, precision-form handle)."""
     m, n = A.shape
     ell = Omega.shape[0]
     out = torch.empty_like(Omega) if out is None else out
-    h.check(lib().nys_sketch(h.h, m, n, NYS_F64, _ptr(_f64(A, "A")), A.stride(0), _ptr(_f64(D, "D")),
+    if A.dtype == torch.float32:
+        if A.stride(1) != 1 or not A.is_cuda:
+            raise TypeError("A must be a row-major CUDA tensor")
+        dt, pa = NYS_F32, _ptr(A)
+    else:
+        dt, pa = NYS_F64, _ptr(_f64(A, "A"))
+    h.check(lib().nys_sketch(h.h, m, n, dt, pa, A.stride(0), _ptr(_f64(D, "D")),
                              ell, _ptr(_f64(Omega, "Omega")), _ptr(_f64(out, "Y")), Omega.shape[1]))
     return out
 

@@ -22,24 +22,68 @@ def nys():
     return N
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (300, 40, 1000), (777, 256, 2048), (1000, 416, 5000),
-                                   (129, 400, 4100), (2000, 100, 20001)])
-def test_tensor_core_gemm_matches_fp64(nys, M, N, K):
+GEMM_SHAPES = [(128, 16, 64), (300, 40, 1000), (777, 256, 2048), (1000, 416, 5000), (129, 400, 4100),
+               (2000, 100, 20001), (513, 96, 256), (3000, 416, 3000), (256, 512, 64)]
+
+
+@pytest.mark.parametrize("kernel", ["0", "1"])
+@pytest.mark.parametrize("M,N,K", GEMM_SHAPES)
+def test_tensor_core_gemm_matches_fp64(nys, monkeypatch, kernel, M, N, K):
     """tcgen05 kind::f16 BF16 products (FP32 accumulation) against an FP64
-    product of the same BF16 values; bound: K * 2^-24 growth on sum |a b|."""
+    product of the same BF16 values; bound: K * 2^-24 growth on sum |a b|.
+    kernel "0": one CTA per 128-row stripe (cta_group::1) with split-K;
+    "1": a CTA pair per 256-row stripe (cta_group::2), k-blocks spread over
+    the resident pairs -- shapes with whole tiles written directly (513 x 96
+    x 256, 256 x 512 x 64) and with tiles summed from several pairs."""
+    monkeypatch.setenv("NYS_UMMA_PAIR", kernel)
     g = torch.Generator().manual_seed(M + N + K)
     ldk = (K + 7) // 8 * 8
     A = torch.zeros(M, ldk, dtype=torch.bfloat16)
     B = torch.zeros(N, ldk, dtype=torch.bfloat16)
     A[:, :K] = (torch.rand(M, K, generator=g) - 0.5).to(torch.bfloat16)
     B[:, :K] = (torch.rand(N, K, generator=g) - 0.5).to(torch.bfloat16)
-    h = nys.Handle(16384, 4096, ell=8)
+    h = nys.Handle(16384, 4096, ell=128)   # workspace for the pair kernel's partial tiles
     Ad, Bd = A.to(DEV), B.to(DEV)
-    C = nys.nys_gemm_bf16(h, Ad[:, :K] if ldk == K else Ad.narrow(1, 0, K), Bd.narrow(1, 0, K)).cpu().double()
+    Av = Ad[:, :K] if ldk == K else Ad.narrow(1, 0, K)
+    C = nys.nys_gemm_bf16(h, Av, Bd.narrow(1, 0, K)).cpu().double()
     ref = (A[:, :K].double() @ B[:, :K].double().T).T
     bound = (A[:, :K].double().abs() @ B[:, :K].double().abs().T).T
     err = (C - ref).abs()
     assert float((err - 4 * K * 2.0 ** -24 * bound).max()) <= 1e-6
+    # deterministic: the same bits on a second call
+    C2 = nys.nys_gemm_bf16(h, Av, Bd.narrow(1, 0, K)).cpu().double()
+    assert torch.equal(C, C2)
+
+
+@pytest.mark.parametrize("kernel", ["0", "1"])
+@pytest.mark.parametrize("m,n,ell", [(300, 1200, 40), (2000, 600, 100), (500, 1200, 400), (1000, 3000, 400)])
+def test_precision_sketch_matches_fp64(nys, monkeypatch, kernel, m, n, ell):
+    """The precision form's sketch (Algorithm 1, second step, on the tensor
+    cores): T = A_b^T Omega_b, T' = BF16(D .* T), Y = A_b T' against the FP64
+    product A_b (D .* (A_b^T Omega_b)) of the same BF16 values.  Bound: the
+    FP32 accumulation of each product (4 K 2^-24 on sums of |a b|) and one
+    BF16 rounding of D .* T (2^-8).  The shapes put the D-scaled BF16 output
+    of the first product on the direct path (300 x 1200, 500 x 1200: whole tiles) and on
+    the summed-partials path (2000 x 600, 1000 x 3000), with one and two MMA
+    chunks (ell 40 / 100 and 400)."""
+    monkeypatch.setenv("NYS_UMMA_PAIR", kernel)
+    rng = np.random.default_rng(m + n + ell)
+    A32 = (rng.standard_normal((m, n)) / np.sqrt(n)).astype(np.float32)
+    D = 10.0 ** rng.uniform(-2, 2, n)
+    Om = rng.standard_normal((m, ell))
+    h = nys.Handle(m, n, ell=ell, precision_mode=1)
+    Y = nys.nys_sketch(h, torch.from_numpy(A32).to(DEV), torch.from_numpy(D).to(DEV),
+                       torch.from_numpy(np.ascontiguousarray(Om.T)).to(DEV)).cpu().numpy().T
+    Ab = torch.from_numpy(A32).bfloat16().double().numpy()
+    Omb = torch.from_numpy(Om).float().bfloat16().double().numpy()
+    T = Ab.T @ Omb
+    Yref = Ab @ (D[:, None] * T)
+    errT = 4 * m * 2.0 ** -24 * (np.abs(Ab.T) @ np.abs(Omb))
+    Tmag = D[:, None] * (np.abs(T) + errT)
+    bound = (np.abs(Ab) @ (2.0 ** -8 * Tmag + D[:, None] * errT)
+             + 4 * n * 2.0 ** -24 * (np.abs(Ab) @ Tmag) * (1 + 2.0 ** -8))
+    assert np.all(np.abs(Y - Yref) <= bound), float(np.max(np.abs(Y - Yref) / bound))
+    assert np.linalg.norm(Y - Yref) <= 1e-2 * np.linalg.norm(Yref)
 
 
 def _qp32(seed, m, n):
