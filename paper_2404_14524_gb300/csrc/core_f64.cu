@@ -221,6 +221,19 @@ __device__ __forceinline__ bool jacobi_needs_rotation(double al, double be, doub
   return fabs(ga) > tol * sqrt(al) * sqrt(be);
 }
 
+// Stopping rule shared by the Jacobi kernels.  A sweep stops the iteration
+// when none of its rotations had a cosine |ga| / sqrt(al be) above 2^-30:
+// cyclic Jacobi converges quadratically, so the cosines left after such a
+// sweep are of order 2^-60, far below the rotation threshold `tol`
+// (~sqrt(m) 2^-53), and the next sweep would rotate nothing.  (The classical
+// rule, a whole sweep without rotations, costs that extra sweep.)  Returns
+// 2 for a rotation above that bound, 1 for one below it.
+__device__ __forceinline__ int jacobi_rotation_level(double al, double be, double ga) {
+  const double ab = al * be;
+  if (ab > 0x1.0p-900 && ab < 0x1.0p+900) return ga * ga > 0x1.0p-60 * ab ? 2 : 1;
+  return fabs(ga) > 0x1.0p-30 * sqrt(al) * sqrt(be) ? 2 : 1;
+}
+
 // Rotation (c, s) that zeroes the inner product (Rutishauser's formulas):
 // zeta = (be - al) / (2 ga), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 // c = 1 / sqrt(1 + t^2), s = c t.  Written as t = 2 ga sign(d) /
@@ -309,15 +322,15 @@ __global__ void __launch_bounds__(kNT) k_jacobi(int m, int ell, double* B, int l
             __stcg(bp + i, c * x - s * y);
             __stcg(bq + i, s * x + c * y);
           }
-          if (tid == 0) rotated = 1;
+          if (tid == 0) rotated |= jacobi_rotation_level(al, be, ga);
         }
       }
       if (!grid_barrier(bar, err)) return;
     }
-    if (tid == 0 && rotated) { atomicOr(sweep_flags + sweep, 1); rotated = 0; }
+    if (tid == 0 && rotated) { atomicOr(sweep_flags + sweep, rotated); rotated = 0; }
     if (!grid_barrier(bar, err)) return;
     const int any = __ldcg(sweep_flags + sweep);
-    if (!any) {
+    if (!(any & 2)) {
       if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep + 1;
       return;
     }
@@ -390,12 +403,12 @@ __global__ void __launch_bounds__(kJT) k_jacobi_smem(int m, int ell, double* B, 
             bp[i] = c * x - sn * y;
             bq[i] = sn * x + c * y;
           }
-          if (lane == 0) rotated = 1;
+          if (lane == 0) atomicOr(&rotated, jacobi_rotation_level(al, be, ga));
         }
       }
       __syncthreads();
     }
-    if (!rotated) break;
+    if (!(rotated & 2)) break;
     __syncthreads();                     // everyone has read `rotated` before it is reset
   }
   for (long long e = tid; e < (long long)m * ell; e += kJT) {
@@ -500,7 +513,7 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
             if (jacobi_needs_rotation(a, b, g, tol)) {
               double c, sn;
               jacobi_rotation(a, b, g, c, sn);
-              rot[0] = c; rot[1] = sn; rot[2] = 1.0;
+              rot[0] = c; rot[1] = sn; rot[2] = (double)jacobi_rotation_level(a, b, g);
             } else {
               rot[2] = 0.0;
             }
@@ -514,7 +527,7 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
             bp[i] = c * x - sn * y;
             bq[i] = sn * x + c * y;
           }
-          mine = 1.0;
+          mine = fmax(mine, rot[2]);
         }
       }
       cl.sync();                         // every rotation of round r is done
@@ -542,8 +555,8 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
     if (tid < C) *cl.map_shared_rank(flags + rank, tid) = mine;
     cl.sync();
     double any = 0.0;
-    for (int k = 0; k < C; ++k) any += flags[k];
-    if (any == 0.0) break;
+    for (int k = 0; k < C; ++k) any = fmax(any, flags[k]);
+    if (any < 2.0) break;
   }
   // the columns of round 0's pairs are current in every CTA: write them back
   {
@@ -569,9 +582,10 @@ __global__ void __launch_bounds__(kJC) k_jacobi_cluster(int m, int ell, double* 
 // nearly orthogonal columns, so the FP64 Jacobi that follows needs two or
 // three sweeps instead of six to nine.  B is scaled by a power of two so that
 // its largest column norm is about 1 (the FP32 copy keeps small columns in
-// range).  The FP32 sweeps stop when no pair needs a rotation or after
-// max_sweeps; a pair needs one when its inner product exceeds kJ32Tol times
-// the geometric mean of its squared norms and also kJ32Noise times the
+// range).  The FP32 sweeps stop after a sweep without a rotation whose
+// cosine exceeds 2^-9 (kJ32Quad), or after max_sweeps; a pair needs a
+// rotation when its inner product exceeds kJ32Tol times the geometric mean
+// of its squared norms and also kJ32Noise times the
 // largest squared column norm (below that, FP32 rounding of the big columns
 // dominates and the FP64 sweeps must decide anyway).
 constexpr int kJ32T = 512;
@@ -579,6 +593,10 @@ constexpr int kJ32W = kJ32T / 32;
 constexpr int kJ32MaxElems = 40960;      // m * ell floats of the copy (160 KB)
 constexpr float kJ32Tol = 1e-5f;
 constexpr float kJ32Noise = 1e-6f;
+// Quadratic stop, as in the FP64 kernels: a sweep whose rotations all had a
+// cosine below 2^-9 (squared: 2^-18) leaves cosines near kJ32Tol, so no
+// confirming sweep follows it.
+constexpr float kJ32Quad = 0x1.0p-18f;
 
 __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, const double* __restrict__ B, int ld,
                                                             double* __restrict__ V, int max_sweeps,
@@ -637,6 +655,7 @@ __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, cons
           float* bp = F + (size_t)p * m;
           float* bq = F + (size_t)q * m;
           float al = 0.0f, be = 0.0f, ga = 0.0f;
+#pragma unroll 4
           for (int i = lane; i < m; i += 32) {
             const float x = bp[i], y = bq[i];
             al = fmaf(x, x, al);
@@ -649,12 +668,18 @@ __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, cons
             be += __shfl_xor_sync(0xffffffffu, be, o);
             ga += __shfl_xor_sync(0xffffffffu, ga, o);
           }
-          if (al > 0.0f && be > 0.0f && fabsf(ga) > kJ32Tol * sqrtf(al) * sqrtf(be) && fabsf(ga) > noise) {
+          // |ga| > tol sqrt(al be), on squares (al, be <= ~1 after the scaling;
+          // a product that underflows is left to the noise test)
+          if (al > 0.0f && be > 0.0f && ga * ga > (kJ32Tol * kJ32Tol) * (al * be) && fabsf(ga) > noise) {
             const float d = be - al;
             const float h = fmaf(d, d, 4.0f * ga * ga);
-            const float t = (2.0f * ga) * copysignf(1.0f, d == 0.0f ? 1.0f : d) / (fabsf(d) + sqrtf(h));
+            // the tangent needs no correct rounding: c and s below are
+            // orthogonal for any t, a slightly wrong angle is undone later
+            const float t = __fdividef((2.0f * ga) * copysignf(1.0f, d == 0.0f ? 1.0f : d), fabsf(d) + sqrtf(h));
             const float c = rsqrtf(fmaf(t, t, 1.0f));
             const float sn = c * t;
+            if (lane == 0) atomicOr(&rotated, ga * ga > kJ32Quad * (al * be) ? 2 : 1);
+#pragma unroll 4
             for (int i = lane; i < m; i += 32) {
               const float x = bp[i], y = bq[i];
               bp[i] = c * x - sn * y;
@@ -667,13 +692,12 @@ __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, cons
               vp[lane] = c * x - sn * y;
               vq[lane] = sn * x + c * y;
             }
-            if (lane == 0) rotated = 1;
           }
         }
       }
       __syncthreads();
     }
-    if (!rotated) break;
+    if (!(rotated & 2)) break;
     __syncthreads();                     // everyone has read `rotated` before it is reset
   }
   // Newton-Schulz in FP64: X <- 1.5 X - 0.5 X (X^T X), twice
