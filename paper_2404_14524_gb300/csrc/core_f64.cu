@@ -738,6 +738,100 @@ __global__ void __launch_bounds__(kJ32T) k_jacobi_f32_start(int m, int ell, cons
   for (int e = tid; e < ell * ell; e += kJ32T) V[e] = X[e];
 }
 
+// FP64 cleanup after the FP32 start, on the Gram matrix instead of on B2:
+// B2 = B V0 has nearly orthogonal columns (cosines at the FP32 start's
+// tolerance), so G = B2^T B2 = S A S with S = diag of the column norms and A
+// within ~1e-5 of the identity.  Two-sided cyclic Jacobi on such a matrix
+// keeps the high relative accuracy of one-sided Jacobi on B2: it depends on
+// the condition of A (about 1), and forming G in FP64 perturbs A by ~m eps.
+// The rotations are those of the one-sided iteration (the same pair order,
+// the same (c, s) from (g_pp, g_qq, g_pq) as from the squared norms and the
+// inner product, the same stopping rule), so B2 V1 with V1 the accumulated
+// rotations is what the FP64 one-sided sweeps on B2 would converge to.  The
+// matrix is ell x ell (ell <= 32): the whole iteration runs in one CTA, no
+// inner products over the m rows and no cluster barriers; the ceil(ell/2)
+// rotations of a round are computed side by side by the lanes of one warp.
+// G's upper triangle is read (the lower one mirrored); V1 is written.
+constexpr int kJG = 512;
+
+__global__ void __launch_bounds__(kJG) k_jacobi_gram(int ell, const double* __restrict__ G, double* __restrict__ V,
+                                                   double tol, int max_sweeps, const int* err, int* sweeps_out) {
+  constexpr int ld = 33;                 // padded column stride
+  __shared__ double Gs[32 * ld], Vs[32 * ld];
+  __shared__ double rc[16], rs[16];
+  __shared__ int rp[16], rq[16], on[16];
+  __shared__ int level;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (*err) return;
+  for (int e = tid; e < ell * ell; e += kJG) {
+    const int i = e % ell, j = e / ell;
+    Gs[j * ld + i] = i <= j ? G[(size_t)j * ell + i] : G[(size_t)i * ell + j];
+    Vs[j * ld + i] = i == j ? 1.0 : 0.0;
+  }
+  const int lp = ell + (ell & 1);
+  const int npairs = lp / 2;
+  const int L = lp - 1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) level = 0;
+    __syncthreads();
+    for (int r = 0; r < L; ++r) {
+      if (wid == 0 && lane < npairs) {
+        int p, q;
+        rr_pair(lane, r, lp, p, q);
+        int rot = 0;
+        double c = 1.0, sn = 0.0;
+        if (q < ell) {
+          const double a = Gs[p * ld + p], b = Gs[q * ld + q], g = Gs[q * ld + p];
+          if (jacobi_needs_rotation(a, b, g, tol)) {
+            jacobi_rotation(a, b, g, c, sn);
+            rot = 1;
+            atomicOr(&level, jacobi_rotation_level(a, b, g));
+          }
+        }
+        rp[lane] = p;
+        rq[lane] = q;
+        rc[lane] = c;
+        rs[lane] = sn;
+        on[lane] = rot;
+      }
+      __syncthreads();
+      // columns p, q of G and of V: M <- M J
+      for (int e = tid; e < 2 * npairs * ell; e += kJG) {
+        const int which = e / (npairs * ell);
+        const int rem = e - which * npairs * ell;
+        const int k = rem / ell, i = rem - k * ell;
+        if (!on[k]) continue;
+        double* M = which ? Vs : Gs;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], sn = rs[k];
+        const double x = M[p * ld + i], y = M[q * ld + i];
+        M[p * ld + i] = c * x - sn * y;
+        M[q * ld + i] = sn * x + c * y;
+      }
+      __syncthreads();
+      // rows p, q of G: G <- J^T G
+      for (int e = tid; e < npairs * ell; e += kJG) {
+        const int k = e / ell, j = e - k * ell;
+        if (!on[k]) continue;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], sn = rs[k];
+        const double x = Gs[j * ld + p], y = Gs[j * ld + q];
+        Gs[j * ld + p] = c * x - sn * y;
+        Gs[j * ld + q] = sn * x + c * y;
+      }
+      __syncthreads();
+    }
+    if (!(level & 2)) break;
+    __syncthreads();                     // everyone has read `level` before it is reset
+  }
+  for (int e = tid; e < ell * ell; e += kJG) {
+    const int i = e % ell, j = e / ell;
+    V[(size_t)j * ell + i] = Vs[j * ld + i];
+  }
+  if (tid == 0) *sweeps_out = sweep < max_sweeps ? sweep + 1 : max_sweeps + 1;
+}
+
 // G[j][j] += f * trace(G)  (one CTA): the shift of the first Cholesky-QR pass.
 __global__ void __launch_bounds__(kNT) k_shift_trace(int ell, double* G, double f) {
   __shared__ double sh[kWarps];
@@ -896,7 +990,9 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
     jm = ell;
     jld = ell;
   }
-  if (direct && cw.f32_start && ell >= 2 && ell <= kJacobiClusterMaxEll && (long long)m * ell <= kJ32MaxElems) {
+  const bool f32 =
+      direct && cw.f32_start && ell >= 2 && ell <= kJacobiClusterMaxEll && (long long)m * ell <= kJ32MaxElems;
+  if (f32) {
     // FP32 Jacobi start: V (orthogonal to FP64 precision) in cw.R, then the
     // FP64 Jacobi runs on B2 = B V
     const size_t sm = sizeof(float) * ((size_t)m * ell + (size_t)ell * ell);
@@ -913,7 +1009,18 @@ cudaError_t nystrom_core_f64(cudaStream_t st, int m, int ell, const double* Y, c
   }
   double tol = sqrt((double)jm) * 0x1.0p-53;
   if (tol < 0x1.0p-52) tol = 0x1.0p-52;
-  if (ell <= kJacobiClusterMaxEll && ell >= 2 && jm <= kJacobiClusterMaxRows) {
+  if (f32 && cw.gram) {
+    // FP64 sweeps on G2 = B2^T B2 (one CTA), then B3 = B2 V1 into Ynu
+    e = gemm_f64(st, ell, ell, m, cw.B2, ld, 1, cw.B2, 1, ld, nullptr, cw.G, 1, ell, cw.split_buf, cw.split_cap);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_jacobi_gram<<<1, kJG, 0, st>>>(ell, cw.G, cw.Rt, tol, CoreWork::kMaxSweeps, err, si + SI_SWEEPS);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = gemm_f64(st, m, ell, ell, cw.B2, 1, ld, cw.Rt, 1, ell, nullptr, cw.Ynu, 1, ld, cw.split_buf,
+                 cw.split_cap);
+    Bsv = cw.Ynu;
+  } else if (ell <= kJacobiClusterMaxEll && ell >= 2 && jm <= kJacobiClusterMaxRows) {
     // one CTA per column pair of a round, in one thread-block cluster
     const int C = (ell + 1) / 2;
     const size_t sm = sizeof(double) * (4 * (size_t)jm + C);

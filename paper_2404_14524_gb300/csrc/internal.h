@@ -99,6 +99,7 @@ struct CoreWork {
   double* split_buf;
   size_t split_cap;
   int f32_start = 1;  // FP32 Jacobi start for small B (NYS_JACOBI_F32=0 turns it off)
+  int gram = 1;       // after it, FP64 sweeps on B^T B in one CTA (NYS_JACOBI_GRAM=0: on B, cluster)
   static constexpr int kMaxSweeps = 40;
 };
 // Algorithm 1 steps 3-8 from a sketch.  Writes U (m x ell, ld), lam (ell) and

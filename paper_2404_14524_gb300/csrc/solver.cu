@@ -1791,6 +1791,7 @@ int nys_create(nys_handle* out, const nys_options* opt, int max_m, int max_n, in
   }
   if (const char* env = std::getenv("NYS_TRACE")) h->trace = (env[0] != '0');
   if (const char* env = std::getenv("NYS_JACOBI_F32")) h->cw.f32_start = (env[0] != '0');
+  if (const char* env = std::getenv("NYS_JACOBI_GRAM")) h->cw.gram = (env[0] != '0');
   if (const char* env = std::getenv("NYS_DEVICE_IPM")) h->use_dev_ipm = (env[0] != '0');
   if (const char* env = std::getenv("NYS_TRACE_TUNE")) h->trace_tune = (env[0] != '0');
   if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->st) != cudaSuccess ||

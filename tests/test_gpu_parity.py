@@ -137,13 +137,14 @@ def test_nystrom_factor_matches_oracle(nys, m, n, ell):
     assert np.linalg.norm(Nh - Nhw, 2) <= 1e-10 * np.linalg.norm(Nhw, 2)
 
 
-@pytest.mark.parametrize("f32_start", ["1", "0"])
-@pytest.mark.parametrize("m,ell,dspan", [(200, 20, 0.0), (150, 30, 12.0), (1024, 32, 6.0)])
-def test_nystrom_factor_with_and_without_the_fp32_jacobi_start(nys, monkeypatch, f32_start, m, ell, dspan):
+@pytest.mark.parametrize("f32_start,gram", [("1", "1"), ("1", "0"), ("0", "1")])
+@pytest.mark.parametrize("m,ell,dspan", [(200, 20, 0.0), (150, 30, 12.0), (1024, 32, 6.0), (120, 12, 16.0)])
+def test_nystrom_factor_with_and_without_the_fp32_jacobi_start(nys, monkeypatch, f32_start, gram, m, ell, dspan):
     """The small direct route starts the FP64 Jacobi from an FP32 Jacobi
-    rotation V (made orthogonal in FP64); either way the factor matches the
-    oracle's (D spanning up to 12 orders of magnitude, as in late IPM
-    iterations)."""
+    rotation V (made orthogonal in FP64), then runs the FP64 sweeps either on
+    the Gram matrix of B V (one CTA; gram "1") or on B V itself (cluster);
+    every way the factor matches the oracle's (D spanning up to 16 orders of
+    magnitude, as in late IPM iterations)."""
     rng = np.random.default_rng(m + ell)
     n = 3 * m
     A = rng.standard_normal((m, n)) / np.sqrt(n)
@@ -152,6 +153,7 @@ def test_nystrom_factor_with_and_without_the_fp32_jacobi_start(nys, monkeypatch,
     Y = O.sketch(A, D, Om)
     Fw = O.nystrom_from_sketch(Y, Om)
     monkeypatch.setenv("NYS_JACOBI_F32", f32_start)
+    monkeypatch.setenv("NYS_JACOBI_GRAM", gram)
     h = nys.Handle(m, n, ell=ell)
     U, lam, nu = nys.nys_nystrom(h, P(Y), P(Om))
     U, lam = U.cpu().numpy().T, lam.cpu().numpy()
