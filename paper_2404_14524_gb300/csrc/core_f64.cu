@@ -240,15 +240,33 @@ __device__ __forceinline__ int jacobi_rotation_level(double al, double be, doubl
 // (|d| + sqrt(d^2 + 4 ga^2)) with d = be - al (the same number, one root and
 // one division instead of two of each; sign(0) = +1 reproduces the sign that
 // zeta = +-0 gives) and c from a reciprocal square root.  For |zeta| > 2^13
-// the first-order angle t = ga / d with c = 1 - t^2 / 2 is used, which is
+// the first-order angle t = ga / d (jacobi_small_tangent) with c = 1 - t^2 / 2
+// is used, which is
 // orthogonal to double precision (c^2 (1 + t^2) = 1 - O(t^4), t^4 < 2^-56);
 // its angle error leaves a residual inner product of relative size
 // 1/(4 zeta^2) for the next sweep.  FP64 divisions and roots cost hundreds of
 // cycles of latency each on this GPU, and a round waits for this chain.
+// t = ga / d for the first-order branch.  The reciprocal of d starts from the
+// FP32 reciprocal (2^-23 relative) and takes one Newton-Raphson step,
+// r <- r (2 - d r), which squares the error (2^-46); exact division where d
+// lies outside FP32's normal range.  The branch's own angle error is
+// 1/(4 zeta^2) < 2^-28 relative, so 2^-46 changes nothing, and c, s below are
+// orthogonal for any t.  (An FP64 division is a chain of several hundred
+// cycles on this GPU, and every Jacobi round waits for it.)
+__device__ __forceinline__ double jacobi_small_tangent(double ga, double d) {
+  const double ad = fabs(d);
+  if (ad > 0x1.0p-120 && ad < 0x1.0p+120) {
+    double r = (double)__frcp_rn((float)d);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return ga * r;
+  }
+  return ga / d;
+}
+
 __device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double& c, double& s) {
   const double d = be - al;
   if (fabs(d) > 16384.0 * fabs(ga)) {
-    const double t = ga / d;
+    const double t = jacobi_small_tangent(ga, d);
     c = fma(-0.5 * t, t, 1.0);
     s = c * t;
     return;
@@ -758,8 +776,9 @@ __global__ void __launch_bounds__(kJG) k_jacobi_gram(int ell, const double* __re
                                                    double tol, int max_sweeps, const int* err, int* sweeps_out) {
   constexpr int ld = 33;                 // padded column stride
   __shared__ double Gs[32 * ld], Vs[32 * ld];
-  __shared__ double rc[16], rs[16];
-  __shared__ int rp[16], rq[16], on[16];
+  __shared__ double rc[2][16], rs[2][16];   // rotations of a round, double-buffered by round parity
+  __shared__ int rp[2][16], rq[2][16], on[2][16];
+  __shared__ unsigned char bk1[136], bk2[136];   // pair blocks (k1 <= k2) of the symmetric update
   __shared__ int level;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (*err) return;
@@ -770,60 +789,89 @@ __global__ void __launch_bounds__(kJG) k_jacobi_gram(int ell, const double* __re
   }
   const int lp = ell + (ell & 1);
   const int npairs = lp / 2;
+  const int nblk = npairs * (npairs + 1) / 2;
   const int L = lp - 1;
-  int sweep = 0;
+  if (tid == 0) {
+    int e = 0;
+    for (int k1 = 0; k1 < npairs; ++k1)
+      for (int k2 = k1; k2 < npairs; ++k2) { bk1[e] = (unsigned char)k1; bk2[e] = (unsigned char)k2; ++e; }
+  }
+  // V <- V J for the rotations in buffer b (threads from `first` on)
+  auto v_update = [&](int b, int first, int stride) {
+    for (int e = tid - first; e >= 0 && e < npairs * ell; e += stride) {
+      const int k = e / ell, i = e - k * ell;
+      if (!on[b][k]) continue;
+      const int p = rp[b][k], q = rq[b][k];
+      const double c = rc[b][k], sn = rs[b][k];
+      const double x = Vs[p * ld + i], y = Vs[q * ld + i];
+      Vs[p * ld + i] = c * x - sn * y;
+      Vs[q * ld + i] = sn * x + c * y;
+    }
+  };
+  int sweep = 0, buf = 0;
+  bool pending = false;                  // the V update of the last round is still to do
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) level = 0;
     __syncthreads();
     for (int r = 0; r < L; ++r) {
-      if (wid == 0 && lane < npairs) {
-        int p, q;
-        rr_pair(lane, r, lp, p, q);
-        int rot = 0;
-        double c = 1.0, sn = 0.0;
-        if (q < ell) {
-          const double a = Gs[p * ld + p], b = Gs[q * ld + q], g = Gs[q * ld + p];
-          if (jacobi_needs_rotation(a, b, g, tol)) {
-            jacobi_rotation(a, b, g, c, sn);
-            rot = 1;
-            atomicOr(&level, jacobi_rotation_level(a, b, g));
+      if (wid == 0) {
+        if (lane < npairs) {
+          int p, q;
+          rr_pair(lane, r, lp, p, q);
+          int rot = 0;
+          double c = 1.0, sn = 0.0;
+          if (q < ell) {
+            const double a = Gs[p * ld + p], bb = Gs[q * ld + q], g = Gs[q * ld + p];
+            if (jacobi_needs_rotation(a, bb, g, tol)) {
+              jacobi_rotation(a, bb, g, c, sn);
+              rot = 1;
+              atomicOr(&level, jacobi_rotation_level(a, bb, g));
+            }
           }
+          rp[buf][lane] = p;
+          rq[buf][lane] = q;
+          rc[buf][lane] = c;
+          rs[buf][lane] = sn;
+          on[buf][lane] = rot;
         }
-        rp[lane] = p;
-        rq[lane] = q;
-        rc[lane] = c;
-        rs[lane] = sn;
-        on[lane] = rot;
+      } else if (pending) {
+        // the previous round's rotations of V, while warp 0 forms this round's
+        v_update(buf ^ 1, 32, kJG - 32);
       }
       __syncthreads();
-      // columns p, q of G and of V: M <- M J
-      for (int e = tid; e < 2 * npairs * ell; e += kJG) {
-        const int which = e / (npairs * ell);
-        const int rem = e - which * npairs * ell;
-        const int k = rem / ell, i = rem - k * ell;
-        if (!on[k]) continue;
-        double* M = which ? Vs : Gs;
-        const int p = rp[k], q = rq[k];
-        const double c = rc[k], sn = rs[k];
-        const double x = M[p * ld + i], y = M[q * ld + i];
-        M[p * ld + i] = c * x - sn * y;
-        M[q * ld + i] = sn * x + c * y;
+      // G <- J^T G J, one 2 x 2 block (rows of pair k1, columns of pair k2,
+      // k1 <= k2) per thread, mirrored below the diagonal
+      for (int e = tid; e < nblk; e += kJG) {
+        const int k1 = bk1[e], k2 = bk2[e];
+        if (!on[buf][k1] && !on[buf][k2]) continue;
+        const int a0 = rp[buf][k1], a1 = rq[buf][k1], b0 = rp[buf][k2], b1 = rq[buf][k2];
+        const double c1 = rc[buf][k1], s1 = rs[buf][k1], c2 = rc[buf][k2], s2 = rs[buf][k2];
+        const bool ra = a1 < ell, rb = b1 < ell;    // the second index of a pair may be the dummy
+        const double g00 = Gs[b0 * ld + a0];
+        const double g01 = rb ? Gs[b1 * ld + a0] : 0.0;
+        const double g10 = ra ? Gs[b0 * ld + a1] : 0.0;
+        const double g11 = (ra && rb) ? Gs[b1 * ld + a1] : 0.0;
+        // X = G J2 (columns), then J1^T X (rows)
+        const double x00 = c2 * g00 - s2 * g01, x01 = s2 * g00 + c2 * g01;
+        const double x10 = c2 * g10 - s2 * g11, x11 = s2 * g10 + c2 * g11;
+        const double y00 = c1 * x00 - s1 * x10, y10 = s1 * x00 + c1 * x10;
+        const double y01 = c1 * x01 - s1 * x11, y11 = s1 * x01 + c1 * x11;
+        Gs[b0 * ld + a0] = y00;
+        Gs[a0 * ld + b0] = y00;
+        if (rb) { Gs[b1 * ld + a0] = y01; Gs[a0 * ld + b1] = y01; }
+        if (ra) { Gs[b0 * ld + a1] = y10; Gs[a1 * ld + b0] = y10; }
+        if (ra && rb) { Gs[b1 * ld + a1] = y11; Gs[a1 * ld + b1] = y11; }
       }
-      __syncthreads();
-      // rows p, q of G: G <- J^T G
-      for (int e = tid; e < npairs * ell; e += kJG) {
-        const int k = e / ell, j = e - k * ell;
-        if (!on[k]) continue;
-        const int p = rp[k], q = rq[k];
-        const double c = rc[k], sn = rs[k];
-        const double x = Gs[j * ld + p], y = Gs[j * ld + q];
-        Gs[j * ld + p] = c * x - sn * y;
-        Gs[j * ld + q] = sn * x + c * y;
-      }
+      pending = true;
+      buf ^= 1;
       __syncthreads();
     }
     if (!(level & 2)) break;
     __syncthreads();                     // everyone has read `level` before it is reset
+  }
+  if (pending) {
+    v_update(buf ^ 1, 0, kJG);
+    __syncthreads();
   }
   for (int e = tid; e < ell * ell; e += kJG) {
     const int i = e % ell, j = e / ell;
