@@ -226,16 +226,39 @@ int nys_solve(nys_handle h, const nys_problem* p, nys_result* r);
  * host memory per problem).  The handle must have been created with
  * max_batch >= 1.  Returns the worst status (negative errors first); each
  * r[i].status holds its own.  All work is complete on return.  A problem's
- * results do not depend on the batch it is in or on the number in flight. */
+ * results do not depend on the batch it is in or on the number in flight;
+ * they depend on its PCG cluster plan, which is the fixed rule's unless the
+ * plan autotuner (nys_batch_plan) has chosen one for its shape bucket. */
 int nys_solve_batched(nys_handle h, int count, const nys_problem* p, nys_result* r);
 
 /* Problems in flight chosen for this handle's batches by timed trials (0
  * until a batch of at least 128 problems with max_batch >= 16 has run on the
- * device-resident path): in-flight counts of 8, 16, 24, 32, 48, 64, ... are
- * scored by the PCG work completed per second over 0.8 s each, a larger
- * count kept only when it beats the best by 3 %.  Untuned batches run
+ * device-resident path): in-flight counts of 8, 16, 24, 32, 48, 64, ..., up
+ * to the number of hardware queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless
+ * set) and max_batch, are scored by the PCG work completed per second over
+ * 0.8 s each, a larger count kept only when it beats the best by 3 %.  Untuned batches run
  * max_batch at once; NYS_BATCH_TUNE=0 keeps max_batch. */
 int nys_batch_inflight(nys_handle h);
+
+/* The PCG cluster plan the batching form's autotuner chose for problems of
+ * this shape (the bucket of m rounded up to 64, n rounded up to 512, the same
+ * ell = min(ell option, m, the problem's ell)).  Before a batch of at least
+ * 128 problems with max_batch >= 16 on the device-resident path starts
+ * (NYS_BATCH_TUNE and NYS_BATCH_PLAN_TUNE not 0), every bucket this handle
+ * has not seen is tuned:
+ * each cluster plan with A in shared memory that fits (16, 8 or 4 CTAs) runs
+ * 16 forced PCG iterations of a synthetic system of the bucket's first
+ * shape, and the plan with the least time x max(CTAs, SMs / hardware queues)
+ * is kept (no more problems run at once than CUDA_DEVICE_MAX_CONNECTIONS
+ * queues, 8 unless set, so a narrower plan is charged that share of the
+ * SMs).  Buckets whose A fits no cluster's shared memory keep the fixed
+ * rule's plan reading A from L2 (*ctas = 0): alone on the GPU a trial finds
+ * A in L2, which a full batch does not.
+ * Later problems of the bucket, in this and later calls, run it when it fits
+ * their exact shape.  Writes *ctas (4, 8, 16; 0 when the bucket keeps the
+ * fixed rule's plan) and *a_smem (1: A in shared memory); returns 1 when the
+ * bucket has been tuned, 0 when not, NYS_ERR_ARG on bad arguments. */
+int nys_batch_plan(nys_handle h, int m, int n, int ell, int* ctas, int* a_smem);
 
 int nys_destroy(nys_handle h);
 

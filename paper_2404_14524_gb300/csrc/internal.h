@@ -235,6 +235,12 @@ struct ClusterPlan {
 // solve, 1 for many solves side by side, 2 the latency plan if one exists,
 // else the throughput plan; false when no cluster fits.
 bool pcg_cluster_plan(int m, int n, int ell, int policy, ClusterPlan* plan);
+// Every cluster plan that fits an m x n system of rank ell (16, 8, 4 CTAs
+// with A on chip, then 8, 4 with A read from L2), at most cap; returns the
+// count.
+int pcg_cluster_candidates(int m, int n, int ell, ClusterPlan* out, int cap);
+// The plan of C CTAs (A on chip if a_smem) for this exact shape, if it fits.
+bool pcg_cluster_plan_for(int m, int n, int ell, int C, int a_smem, ClusterPlan* plan);
 // One system (`task`, tasks == nullptr) or `count` systems from the device
 // array `tasks`, each planned no larger than `plan`.
 cudaError_t pcg_cluster_f64(cudaStream_t st, const ClusterPlan& plan, const ClusterPcgTask& task,

@@ -546,6 +546,35 @@ bool pcg_cluster_plan(int m, int n, int ell, int policy, ClusterPlan* plan) {
   return false;
 }
 
+int pcg_cluster_candidates(int m, int n, int ell, ClusterPlan* out, int cap) {
+  if (m <= 0 || n <= 0 || ell <= 0) return 0;
+  static const int Cs[3] = {kMaxC, 8, 4};
+  int k = 0;
+  for (int as = 1; as >= 0; --as)
+    for (int ci = 0; ci < 3 && k < cap; ++ci) {
+      if (as == 0 && Cs[ci] == kMaxC) continue;   // A from L2 runs on 8 or 4 CTAs only
+      const Layout L = make_layout(m, n, ell, Cs[ci], as != 0);
+      const size_t bytes = L.total * sizeof(double);
+      if (bytes > kSmemCap || !launchable(Cs[ci], bytes, as != 0)) continue;
+      out[k].C = Cs[ci];
+      out[k].a_smem = as;
+      out[k].smem_bytes = bytes;
+      ++k;
+    }
+  return k;
+}
+
+bool pcg_cluster_plan_for(int m, int n, int ell, int C, int a_smem, ClusterPlan* plan) {
+  if (m <= 0 || n <= 0 || ell <= 0 || (C != 4 && C != 8 && C != kMaxC)) return false;
+  const Layout L = make_layout(m, n, ell, C, a_smem != 0);
+  const size_t bytes = L.total * sizeof(double);
+  if (bytes > kSmemCap || !launchable(C, bytes, a_smem != 0)) return false;
+  plan->C = C;
+  plan->a_smem = a_smem;
+  plan->smem_bytes = bytes;
+  return true;
+}
+
 cudaError_t pcg_cluster_f64(cudaStream_t st, const ClusterPlan& plan, const ClusterPcgTask& task,
                             const ClusterPcgTask* tasks, int count) {
   const void* fn = plan.a_smem ? (const void*)k_pcg_cluster<true> : (const void*)k_pcg_cluster<false>;

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -141,6 +142,11 @@ struct nys_solver {
   unsigned ipm_kernels_top = 0, ipm_kernels_body = 0;
   bool use_dev_ipm = true;             // NYS_DEVICE_IPM=0 keeps the host-driven iteration
   int tuned_inflight = 0;              // batching form: problems in flight chosen by the autotuner
+  // batching form: cluster plan (CTAs, A on chip) per shape bucket chosen by
+  // timed trials (C = 0: no cluster plan fits), and the trials' buffer
+  std::map<long long, std::pair<int, int>> tuned_plans;
+  double* tune_buf = nullptr;
+  size_t tune_cap = 0;
   int trace_tune = 0;                  // NYS_TRACE_TUNE=1: the autotuner's trials on stderr
   // batching form: worker solvers (created on first use), one per in-flight QP
   int max_batch = 0;
@@ -1822,6 +1828,7 @@ int nys_destroy(nys_handle h) {
   if (h->ev_b1) cudaEventDestroy(h->ev_b1);
   if (h->d_tasks) cudaFree(h->d_tasks);
   if (h->h_tasks) cudaFreeHost(h->h_tasks);
+  if (h->tune_buf) cudaFree(h->tune_buf);
   cudaFree(h->arena);
   if (h->lp_arena) cudaFree(h->lp_arena);
   if (h->stage) cudaFree(h->stage);
@@ -2052,12 +2059,142 @@ void host_run(IpmRun& run) {
 // each by the PCG work it completed per second (PCG iterations x m x n),
 // stops after two counts that do not beat the best by kTuneMargin, and keeps
 // the best for the rest of the call and for later calls
-// (nys_batch_inflight reports it).  Batches of fewer than 128 problems are
+// (nys_batch_inflight reports it).  Counts above the number of hardware
+// queues are not tried.  Batches of fewer than 128 problems are
 // too short to tune and run max_batch at once.  Each problem's arithmetic depends on its
-// own launch plan only, so the choice never changes a result.
+// own launch plan only, so the in-flight count never changes a result.
 constexpr double kTuneSettle = 0.1;
 constexpr double kTuneWindow = 0.8;
 constexpr double kTuneMargin = 1.03;   // a larger count must beat the best by 3 %
+
+// Cluster-plan autotuning of the batching form.  Problems are grouped in
+// shape buckets (m rounded up to 64, n to 512, the same ell); for a bucket
+// not seen before, every cluster plan with A on chip that fits its first
+// problem's shape (16, 8 or 4 CTAs) runs kTunePcg
+// forced PCG iterations of a system of that shape (Gaussian A, D = 1, U = 0,
+// lam = 1, xi = 1, delta = 1: the work does not depend on the values), once
+// to warm up and twice timed with CUDA events, and the plan with the least
+// cost time x max(CTAs, SMs / hardware queues) is kept for the bucket, for
+// this call and later ones.  The SMs are what the problems of a full batch
+// share, but no more problems run at once than there are hardware queues
+// (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless set), so a plan narrower than
+// SMs / queues leaves SMs idle and is charged as if it used that share
+// (time x CTAs alone picked 4-CTA plans for most of the 256-QP workload and
+// ran it at 9.4 instead of 13.9 QP/s).  The trials run before any problem
+// starts, on an otherwise idle GPU.  A problem runs the bucket's plan when
+// it fits its exact shape, else the fixed rule's.  Buckets whose A fits no
+// cluster's shared memory keep the fixed rule's plan (8 or 4 CTAs reading A
+// from L2): a trial alone on the GPU finds A in L2, but under a full batch
+// the problems' matrices compete for L2 and such plans run from DRAM, so
+// the trials misjudge them (with them in the trials the 256-QP workload ran
+// at 11.4 QP/s).
+//
+// Measured on the 256-QP workload (m <= 1024, 32 hardware queues): with 32
+// in flight, 13.86 QP/s on the fixed rule's plans and 13.94 with the tuner
+// (19 of 81 buckets retuned, mostly to 4 CTAs); with 64 in flight, 11.7
+// against 12.0; earlier forms of the tuner ran it at 9.4 (cost time x CTAs,
+// L2 plans included: 4-CTA L2 plans for 62 buckets) and 11.4 QP/s
+// (queue-aware cost, L2 plans included).  NYS_BATCH_PLAN_TUNE=0 turns it
+// off.
+constexpr int kTunePcg = 16;
+
+long long plan_bucket(int m, int n, int ell) {
+  return ((long long)((m + 63) / 64) << 40) | ((long long)((n + 511) / 512) << 20) | (long long)ell;
+}
+
+int batch_ell(const nys_solver* h, const nys_problem& q) {
+  return std::min(std::min(h->ell_cap, q.m), q.ell > 0 ? q.ell : h->ell_cap);
+}
+
+int tune_plans(nys_solver* h, int count, const nys_problem* p) {
+  int queues = 8;
+  if (const char* env = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS")) {
+    const int v = std::atoi(env);
+    if (v > 0) queues = v;
+  }
+  const double min_ctas = (double)h->num_sms / queues;
+  for (int i = 0; i < count; ++i) {
+    const int m = p[i].m, n = p[i].n, ell = batch_ell(h, p[i]);
+    if (m <= 0 || n <= 0 || ell <= 0 || m > h->max_m || n > h->max_n) continue;
+    const long long key = plan_bucket(m, n, ell);
+    if (h->tuned_plans.count(key)) continue;
+    ClusterPlan all[6], cand[6];
+    const int na = pcg_cluster_candidates(m, n, ell, all, 6);
+    int nc = 0;
+    for (int k = 0; k < na; ++k)
+      if (all[k].a_smem) cand[nc++] = all[k];
+    if (nc <= 1) {                       // nothing to choose between (or A off chip: the rule)
+      h->tuned_plans[key] = {nc == 1 ? cand[0].C : 0, nc == 1 ? cand[0].a_smem : 0};
+      continue;
+    }
+    const size_t need = (size_t)m * n + n + 2 * (size_t)m + ell + (size_t)m * ell + SD_COUNT + 4;
+    if (need > h->tune_cap) {
+      if (h->tune_buf) cudaFree(h->tune_buf);
+      h->tune_buf = nullptr;
+      h->tune_cap = 0;
+      CK(cudaMalloc(&h->tune_buf, sizeof(double) * need));
+      h->tune_cap = need;
+    }
+    double* A = h->tune_buf;
+    double* D = A + (size_t)m * n;
+    double* xi = D + n;
+    double* x = xi + m;
+    double* lam = x + m;
+    double* U = lam + ell;
+    double* sd = U + (size_t)m * ell;
+    int* iw = reinterpret_cast<int*>(sd + SD_COUNT);   // iterations, error word
+    CK(gaussian_omega(h->st, 0x5eedULL, 0, n, m, A, n));   // n x m column-major = m x n row-major
+    CK(fill_f64(h->st, n, 1.0, D));
+    CK(fill_f64(h->st, m, 1.0, xi));
+    CK(fill_f64(h->st, ell, 1.0, lam));
+    CK(cudaMemsetAsync(U, 0, sizeof(double) * (size_t)m * ell, h->st));
+    ClusterPcgTask t{};
+    t.m = m; t.n = n; t.ell = ell; t.ld = m; t.lda = n;
+    t.A = A; t.D = D; t.U = U; t.lam = lam; t.xi = xi;
+    t.delta = 1.0; t.eta2 = 0.0;
+    t.max_iter = kTunePcg; t.forced = kTunePcg;
+    t.x = x; t.iters = iw; t.sd = sd; t.err = iw + 1; t.t_ns = nullptr;
+    int best = -1;
+    double best_score = 0.0;
+    for (int k = 0; k < nc; ++k) {
+      CK(cudaMemsetAsync(iw, 0, 2 * sizeof(int), h->st));
+      bool ok = pcg_cluster_f64(h->st, cand[k], t, nullptr, 0) == cudaSuccess;
+      ok = ok && cudaEventRecord(h->ev_pcg0, h->st) == cudaSuccess;
+      for (int rep = 0; ok && rep < 2; ++rep) ok = pcg_cluster_f64(h->st, cand[k], t, nullptr, 0) == cudaSuccess;
+      ok = ok && cudaEventRecord(h->ev_pcg1, h->st) == cudaSuccess;
+      if (!ok) { cudaGetLastError(); continue; }
+      CK(cudaStreamSynchronize(h->st));
+      int werr = 0;
+      CK(cudaMemcpy(&werr, iw + 1, sizeof(int), cudaMemcpyDeviceToHost));
+      float ms = 0.f;
+      if (werr != 0 || cudaEventElapsedTime(&ms, h->ev_pcg0, h->ev_pcg1) != cudaSuccess) { cudaGetLastError(); continue; }
+      const double score = 0.5 * ms * std::max((double)cand[k].C, min_ctas);
+      if (h->trace_tune)
+        std::fprintf(stderr, "plan tune m=%d n=%d ell=%d C=%d a_smem=%d ms=%.4f score=%.4f\n", m, n, ell, cand[k].C,
+                     cand[k].a_smem, 0.5 * ms, score);
+      if (best < 0 || score < best_score) { best = k; best_score = score; }
+    }
+    h->tuned_plans[key] = best >= 0 ? std::make_pair(cand[best].C, cand[best].a_smem) : std::make_pair(0, 0);
+  }
+  return NYS_OK;
+}
+
+// The bucket's tuned plan for worker w's next problem, when one is cached
+// and fits the exact shape; otherwise the fixed rule's (recomputed on use).
+void apply_tuned_plan(nys_solver* h, nys_solver* w, int m, int n, int ell) {
+  auto it = h->tuned_plans.find(plan_bucket(m, n, ell));
+  ClusterPlan pl;
+  if (it != h->tuned_plans.end() && it->second.first > 0 &&
+      pcg_cluster_plan_for(m, n, ell, it->second.first, it->second.second, &pl)) {
+    w->cp = pl;
+    w->cp_ok = true;
+    w->cp_m = m;
+    w->cp_n = n;
+    w->cp_ell = ell;
+  } else {
+    w->cp_m = -1;
+  }
+}
 
 int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, const std::vector<int>& order,
                  int want) {
@@ -2074,6 +2211,7 @@ int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, 
         r[pi].status = run.status;
         continue;
       }
+      apply_tuned_plan(h, h->workers[t], run.m, run.n, run.ell);
       if (!run.device_eligible()) {
         host_run(run);
         continue;
@@ -2098,12 +2236,29 @@ int batch_device(nys_solver* h, int count, const nys_problem* p, nys_result* r, 
   int limit = want;
   bool tune_env = true;
   if (const char* env = std::getenv("NYS_BATCH_TUNE")) tune_env = env[0] != '0';
+  bool plan_env = true;                           // cluster plans per shape bucket (above)
+  if (const char* env = std::getenv("NYS_BATCH_PLAN_TUNE")) plan_env = env[0] != '0';
+  if (plan_env && tune_env && want >= 16 && count >= 128) {
+    const int rc = tune_plans(h, count, p);
+    if (rc != NYS_OK) return rc;
+  }
   if (h->tuned_inflight > 0) {
     limit = std::min(h->tuned_inflight, want);
   } else if (tune_env && want >= 16 && count >= 128) {
+    // no more than the hardware queues: beyond them problems only wait behind
+    // one another, and a window's score (work of problems started in earlier
+    // windows included) can reward a larger count by chance (a 64 in flight
+    // once scored 2.1e11 against 1.5e11 for 32 and 48, and then ran the batch
+    // at 11.7 instead of 13.9 QP/s)
+    int queues = 8;
+    if (const char* env = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS")) {
+      const int v = std::atoi(env);
+      if (v > 0) queues = v;
+    }
+    const int top = std::min(want, std::max(8, queues));
     for (int c : {8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512})
-      if (c < want) cand.push_back(c);
-    cand.push_back(want);
+      if (c < top) cand.push_back(c);
+    cand.push_back(top);
     tuning = true;
     limit = cand[0];
   }
@@ -2366,6 +2521,20 @@ int nys_adjoint(nys_handle h, int count, const nys_problem* p, const nys_result*
 int nys_batch_inflight(nys_handle h) {
   if (!h) return NYS_ERR_ARG;
   return h->tuned_inflight;
+}
+
+int nys_batch_plan(nys_handle h, int m, int n, int ell, int* ctas, int* a_smem) {
+  if (!h) return NYS_ERR_ARG;
+  if (m <= 0 || n <= 0 || ell <= 0 || !ctas || !a_smem) return fail(h, NYS_ERR_ARG, "nys_batch_plan: bad argument");
+  auto it = h->tuned_plans.find(plan_bucket(m, n, ell));
+  if (it == h->tuned_plans.end()) {
+    *ctas = 0;
+    *a_smem = 0;
+    return 0;
+  }
+  *ctas = it->second.first;
+  *a_smem = it->second.second;
+  return 1;
 }
 
 int nys_pcg_route(nys_handle h, int m, int n, int ell) {

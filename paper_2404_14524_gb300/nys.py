@@ -116,6 +116,7 @@ _SIGS = {
     "nys_gemm_bf16": (_I, [_P, _I, _I, _I, _P, _LL, _P, _LL, _P, _LL]),
     "nys_solve_batched": (_I, [_P, _I, ctypes.POINTER(Problem), ctypes.POINTER(Result)]),
     "nys_batch_inflight": (_I, [_P]),
+    "nys_batch_plan": (_I, [_P, _I, _I, _I, _P, _P]),
     "nys_adjoint": (_I, [_P, _I, ctypes.POINTER(Problem), ctypes.POINTER(Result), _P, _D, _P, _P, _P, _P]),
 }
 
@@ -564,6 +565,15 @@ def qp_solve(A, b, c, q, x0, y0, z0, handle, eta: float = 1e-12):
 def nys_batch_inflight(h: Handle) -> int:
     """Problems in flight the handle's batch autotuner chose (0: not tuned yet)."""
     return int(lib().nys_batch_inflight(h.h))
+
+
+def nys_batch_plan(h: Handle, m: int, n: int, ell: int):
+    """(tuned, ctas, a_smem): the PCG cluster plan the handle's batch
+    autotuner chose for the shape bucket of (m, n, ell)."""
+    c, a = ctypes.c_int(), ctypes.c_int()
+    rc = lib().nys_batch_plan(h.h, m, n, ell, ctypes.byref(c), ctypes.byref(a))
+    h.check(rc)
+    return rc == 1, c.value, a.value
 
 
 def nys_solve_batched(h: Handle, problems, check: bool = True, forced=None, pcg_log_cap: int = 4096):
